@@ -1,0 +1,192 @@
+"""Seeded synthetic baseband voltages for the CHIME/FRB fan-beam path.
+
+This module is the input generator shared by the tests, the benchmark and the
+smoke check.  It holds none of the beamformer's arithmetic: it only models the
+sky signal and the F-engine quantiser, and writes packed bytes.
+
+Input format (Sec. 2 and Table 1: 2048 inputs, 4-bit real + 4-bit imaginary
+per sample, one sample per 2.56 us):
+
+* one byte per (time, input); the high nibble is the real part and the low
+  nibble the imaginary part, each offset-encoded as ``value + 8``;
+* inside a time sample the 2048 bytes are ordered cylinder-major, then feed,
+  then polarisation: ``byte = (cyl * 256 + feed) * 2 + pol``;
+* a channel's block is ``[T][2048]`` and a multi-channel request stacks them
+  as ``[n_chan][T][2048]``.
+
+Signal model (used only to make realistic test inputs):
+
+* noise: real and imaginary parts i.i.d. N(0, sigma^2), rounded to the nearest
+  integer (ties to even) and clipped to [-7, 7];
+* a source in direction (u, s) (E-W and N-S direction cosines) arrives at
+  cylinder ``c``, feed ``n`` with phase ``exp(+2 pi i f (c D u + n d s) / c0)``,
+  added before quantisation;
+* a dispersed burst has a Gaussian envelope with a complex-Gaussian carrier, a
+  per-channel arrival delay ``k_DM DM (f^-2 - f_ref^-2)`` and the intra-channel
+  dispersive chirp applied in the Fourier domain of the channel's series.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import Iterable, List, Optional, Sequence
+
+import numpy as np
+
+C0 = 299_792_458.0            # speed of light, m/s
+K_DM = 4.148808e3             # dispersion constant, s MHz^2 / (pc cm^-3)
+N_CYL, N_FEED, N_POL = 4, 256, 2
+N_INPUT = N_CYL * N_FEED * N_POL
+FEED_SPACING_M = 0.3048       # N-S feed spacing (Sec. 1)
+CYL_SPACING_M = 20.0          # E-W cylinder spacing (cylinder width, Sec. 1)
+DT_S = 2.56e-6                # sample cadence (Table 1)
+CHAN_BW_HZ = 390625.0         # coarse channel width, 400 MHz / 1024
+
+
+def encode(re: np.ndarray, im: np.ndarray) -> np.ndarray:
+    """Offset-encode integer parts in [-8, 7] into one byte each."""
+    re = np.asarray(re, dtype=np.int16)
+    im = np.asarray(im, dtype=np.int16)
+    if re.min(initial=0) < -8 or re.max(initial=0) > 7 or im.min(initial=0) < -8 or im.max(initial=0) > 7:
+        raise ValueError("4-bit parts must lie in [-8, 7]")
+    return (((re + 8) << 4) | (im + 8)).astype(np.uint8)
+
+
+def quantize(z: np.ndarray, clip: int = 7) -> np.ndarray:
+    """Round re/im to the nearest integer, clip to [-clip, clip], encode."""
+    re = np.clip(np.rint(z.real), -clip, clip).astype(np.int16)
+    im = np.clip(np.rint(z.imag), -clip, clip).astype(np.int16)
+    return encode(re, im)
+
+
+def geometric_phase(freq_hz: float, u: float, s: float,
+                    feed_spacing: float = FEED_SPACING_M,
+                    cyl_spacing: float = CYL_SPACING_M) -> np.ndarray:
+    """Per-input complex gain [2048] of a unit plane wave from (u, s)."""
+    c = np.arange(N_CYL, dtype=np.float64)[:, None, None]
+    n = np.arange(N_FEED, dtype=np.float64)[None, :, None]
+    path = (c * cyl_spacing * u + n * feed_spacing * s) / C0 * freq_hz
+    ph = np.exp(2j * np.pi * np.mod(path, 1.0))
+    return np.broadcast_to(ph, (N_CYL, N_FEED, N_POL)).reshape(N_INPUT)
+
+
+@dataclasses.dataclass
+class PlaneWave:
+    """Point source with a random per-sample phase, independent per pol."""
+    amplitude: float
+    u: float                  # E-W direction cosine
+    s: float                  # N-S direction cosine (sin of zenith angle)
+
+
+@dataclasses.dataclass
+class Burst:
+    """Dispersed burst: Gaussian envelope of ``fwhm_s``, complex carrier."""
+    amplitude: float
+    u: float
+    s: float
+    dm: float                 # pc cm^-3
+    t0_s: float               # arrival time at ``f_ref_hz``
+    fwhm_s: float = 1e-3
+    f_ref_hz: float = 650e6
+
+
+def burst_series(b: Burst, freq_hz: float, n_samples: int,
+                 rng: np.random.Generator) -> np.ndarray:
+    """Complex baseband series [T] of a burst in one coarse channel."""
+    t = np.arange(n_samples) * DT_S
+    delay = K_DM * b.dm * ((freq_hz / 1e6) ** -2 - (b.f_ref_hz / 1e6) ** -2)
+    sig = b.fwhm_s / (2.0 * math.sqrt(2.0 * math.log(2.0)))
+    env = np.exp(-0.5 * ((t - b.t0_s - delay) / sig) ** 2)
+    carrier = (rng.standard_normal(n_samples) + 1j * rng.standard_normal(n_samples)) / math.sqrt(2.0)
+    x = b.amplitude * env * carrier
+    if b.dm != 0.0 and env.max() > 1e-12:
+        # Intra-channel dispersion: group delay falls with baseband frequency nu.
+        nu = np.fft.fftfreq(n_samples, d=DT_S)
+        k = K_DM * 1e12 * b.dm            # s Hz^2
+        phase = 2.0 * np.pi * k * nu ** 2 / (freq_hz ** 2 * (freq_hz + nu))
+        x = np.fft.ifft(np.fft.fft(x) * np.exp(1j * phase))
+    return x
+
+
+def make_voltages(freqs_hz: Sequence[float], n_samples: int, seed: int,
+                  sigma: float = 2.5,
+                  plane_waves: Iterable[PlaneWave] = (),
+                  bursts: Iterable[Burst] = (),
+                  chunk: int = 2048) -> np.ndarray:
+    """Packed voltages ``uint8[n_chan][n_samples][2048]`` for the given channels.
+
+    Deterministic in ``seed``; generated in time chunks to bound memory.
+    """
+    plane_waves = list(plane_waves)
+    bursts = list(bursts)
+    out = np.empty((len(freqs_hz), n_samples, N_INPUT), dtype=np.uint8)
+    root = np.random.default_rng(seed)
+    for ci, f in enumerate(freqs_hz):
+        rng = np.random.default_rng(root.integers(0, 2**63))
+        pw_gain = [geometric_phase(f, p.u, p.s) * p.amplitude for p in plane_waves]
+        b_series = [(burst_series(b, f, n_samples, rng), geometric_phase(f, b.u, b.s))
+                    for b in bursts]
+        for t0 in range(0, n_samples, chunk):
+            t1 = min(n_samples, t0 + chunk)
+            nt = t1 - t0
+            z = rng.standard_normal((nt, N_INPUT), dtype=np.float32) * sigma \
+                + 1j * (rng.standard_normal((nt, N_INPUT), dtype=np.float32) * sigma)
+            for g in pw_gain:
+                # random per-sample phase, independent per polarisation
+                ph = np.exp(2j * np.pi * rng.random((nt, 1, 1, N_POL)))
+                z += (ph * g.reshape(1, N_CYL, N_FEED, N_POL)).reshape(nt, N_INPUT)
+            for series, g in b_series:
+                seg = series[t0:t1]
+                if np.abs(seg).max(initial=0.0) > 1e-9:
+                    z += seg[:, None] * g[None, :]
+            out[ci, t0:t1] = quantize(z)
+    return out
+
+
+# --- the workloads used by tests and the benchmark -------------------------
+
+def config_point_source(seed: int = 0):
+    """1 channel at 600 MHz, 3072 samples, plane wave at 20 deg N-S, 0.5 deg E-W."""
+    freqs = [600e6]
+    pw = PlaneWave(1.5, u=math.sin(math.radians(0.5)), s=math.sin(math.radians(20.0)))
+    raw = make_voltages(freqs, 3072, seed, plane_waves=[pw])
+    return raw, np.array(freqs)
+
+
+def burst_amplitude(n_chan: int, sigma: float = 2.5, snr: float = 20.0) -> float:
+    """Per-input burst amplitude giving nominal S/N ``snr`` in a 1 ms boxcar."""
+    return math.sqrt(snr * sigma * sigma / (1024.0 * math.sqrt(390.0 * 2.0 * n_chan)))
+
+
+def config_node_slice(seed: int = 0, n_samples: int = 49152):
+    """4 channels (410/520/650/790 MHz), 49152 samples, one DM-500 burst."""
+    freqs = [410e6, 520e6, 650e6, 790e6]
+    rng = np.random.default_rng(seed + 1)
+    m = int(rng.integers(0, 256))
+    j = int(rng.integers(0, 4))
+    s = (m - 127.5) / 128.0
+    u = math.sin(math.radians([-0.6, -0.2, 0.2, 0.6][j]))
+    b = Burst(burst_amplitude(len(freqs)), u=u, s=s, dm=500.0,
+              t0_s=0.5 * n_samples * DT_S, f_ref_hz=650e6)
+    raw = make_voltages(freqs, n_samples, seed, bursts=[b])
+    return raw, np.array(freqs), {"burst_beam": 256 * j + m, "burst_chan": 2}
+
+
+def noise_only(freqs_hz: Sequence[float], n_samples: int, seed: int, sigma: float = 2.5) -> np.ndarray:
+    return make_voltages(freqs_hz, n_samples, seed, sigma=sigma)
+
+
+def quantized_noise_variance(sigma: float = 2.5, clip: int = 7) -> float:
+    """Exact variance of clip(round(N(0, sigma^2)), +-clip), by summation."""
+    from math import erf, sqrt
+    cdf = lambda x: 0.5 * (1.0 + erf(x / (sigma * sqrt(2.0))))
+    var = 0.0
+    for k in range(-clip, clip + 1):
+        if k == -clip:
+            p = cdf(k + 0.5)
+        elif k == clip:
+            p = 1.0 - cdf(k - 0.5)
+        else:
+            p = cdf(k + 0.5) - cdf(k - 0.5)
+        var += p * k * k
+    return var

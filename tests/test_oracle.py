@@ -1,0 +1,361 @@
+"""Pins for the FP64 oracle: closed forms, library routines, invariants,
+brute force on tiny geometries, and the paper's stated facts (Table 1,
+Sec. 3.1, Sec. 3.3).  None of these re-types the oracle's own formulas."""
+import cmath
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle.chime_fftbf as O
+from paper_1702_04728_gb300 import synth
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+rng = np.random.default_rng(1234)
+
+
+def gold(name):
+    with open(os.path.join(GOLD, name)) as f:
+        return json.load(f)
+
+
+def rand_raw(shape, clip=7):
+    re = rng.integers(-clip, clip + 1, size=shape)
+    im = rng.integers(-clip, clip + 1, size=shape)
+    return synth.encode(re, im)
+
+
+# --- a0 unpack ------------------------------------------------------------------------
+
+def test_unpack_examples():
+    ex = gold("unpack_examples.json")["examples"]
+    b = np.array([e["byte"] for e in ex], dtype=np.uint8)
+    raw = np.zeros((len(b), 2048), np.uint8)
+    raw[:, 0] = b
+    z = O.unpack(raw)[:, 0, 0, 0]
+    assert np.array_equal(z.real, [e["re"] for e in ex])
+    assert np.array_equal(z.imag, [e["im"] for e in ex])
+
+
+def test_unpack_is_bijection_onto_4bit_grid():
+    raw = np.zeros((256, 2048), np.uint8)
+    raw[:, 5] = np.arange(256)
+    z = O.unpack(raw)[:, 0, 2, 1]          # input 5 = (cyl 0, feed 2, pol 1)
+    pairs = {(int(a.real), int(a.imag)) for a in z}
+    assert pairs == {(r, i) for r in range(-8, 8) for i in range(-8, 8)}
+    # the generator's encoder is the inverse
+    re, im = z.real.astype(int), z.imag.astype(int)
+    assert np.array_equal(synth.encode(re, im), np.arange(256, dtype=np.uint8))
+
+
+def test_unpack_input_order():
+    # byte (c*256 + n)*2 + p carries (cyl c, feed n, pol p)
+    raw = np.full((1, 2048), 0x88, np.uint8)
+    c, n, p = 2, 77, 1
+    raw[0, (c * 256 + n) * 2 + p] = 0x9A
+    z = O.unpack(raw)[0]
+    nz = np.argwhere(z != 0)
+    assert nz.tolist() == [[c, n, p]] and z[c, n, p] == 1 + 2j
+
+
+# --- clamp table (Eq. 1) -------------------------------------------------------------
+
+def nearest_beam_bins(freq, ns_sin, g=O.CHIME):
+    """Nearest-neighbour search over every zero-padded beam (and its aliases)."""
+    M = g.n_bins
+    out = []
+    for s in ns_sin:
+        best, best_d = None, None
+        for L in range(-2 * M, 2 * M + 1):
+            s_beam = L * O.C0 / (M * freq * g.feed_spacing_m)   # beam L steers here
+            d = abs(s_beam - s)
+            if best_d is None or d < best_d - 1e-12:
+                best, best_d = L, d
+        out.append(best % M)
+    return np.array(out)
+
+
+@pytest.mark.parametrize("freq", [400.390625e6, 410e6, 491e6, 520e6, 600e6, 650e6, 790e6, 799.6e6])
+def test_lut_is_nearest_formed_beam(freq):
+    ns = O.default_ns_sin()
+    assert np.array_equal(O.clamp_lut(freq, ns), nearest_beam_bins(freq, ns))
+
+
+def test_lut_custom_pointings_nearest():
+    ns = np.sort(rng.uniform(-1, 1, size=256))
+    assert np.array_equal(O.clamp_lut(700e6, ns), nearest_beam_bins(700e6, ns))
+
+
+def test_lut_eq2_incremental_update():
+    # Eq. (2): moving from f_k to f_k + df shifts each index by N P df d sin(theta)/c;
+    # after rounding the two indices differ from that shift by less than 1.
+    ns = O.default_ns_sin()
+    f0, df = 600e6, 390625.0 * 7
+    L0 = np.floor(O.clamp_arg(f0, ns) + 0.5)
+    L1 = np.floor(O.clamp_arg(f0 + df, ns) + 0.5)
+    shift = 512 * df * 0.3048 * ns / O.C0
+    assert np.all(np.abs((L1 - L0) - shift) < 1.0)
+    assert np.array_equal(np.mod(L1, 512).astype(int), O.clamp_lut(f0 + df, ns))
+
+
+def test_aliasing_onset_matches_paper():
+    t = gold("table1.json")
+    onset = O.C0 / (2 * 0.3048)                       # spacing = half a wavelength
+    assert abs(onset - t["aliasing_onset_hz_approx"]) < 0.02 * onset
+    ns = O.default_ns_sin()
+    below = np.floor(O.clamp_arg(onset * 0.99, ns) + 0.5)
+    above = np.floor(O.clamp_arg(onset * 1.06, ns) + 0.5)
+    assert below.min() >= -256 and below.max() < 256           # no wrap below onset
+    assert above.min() < -256 or above.max() >= 256             # wraps above it
+    assert len(set(O.clamp_lut(onset * 0.99, ns).tolist())) == 256
+    assert len(set(O.clamp_lut(600e6, ns).tolist())) < 256    # aliased duplicates
+
+
+def test_lut_fig1_chromatic_spacing():
+    # Fig. 1: formed beams crowd together at high frequency; the clamp keeps the
+    # selected beam within half a beam spacing of its pointing at every frequency.
+    ns = O.default_ns_sin()
+    for f in np.linspace(400e6, 800e6, 9):
+        L = np.floor(O.clamp_arg(f, ns) + 0.5)
+        s_sel = L * O.C0 / (512 * f * 0.3048)
+        assert np.all(np.abs(s_sel - ns) <= O.C0 / (2 * 512 * f * 0.3048) + 1e-12)
+
+
+# --- a1 N-S beams ---------------------------------------------------------------------
+
+def all_bins_lut():
+    return np.arange(512)
+
+
+def test_ns_matches_numpy_fft():
+    x = O.unpack(rand_raw((3, 2048)))
+    X = O.ns_beams(x, all_bins_lut())                  # [t, c, p, 512]
+    ref = np.fft.fft(np.moveaxis(x, 2, 3), n=512, axis=-1)
+    assert np.allclose(X, ref, rtol=0, atol=1e-9)
+    lut = O.clamp_lut(650e6)
+    assert np.allclose(O.ns_beams(x, lut), ref[..., lut], rtol=0, atol=1e-9)
+
+
+def test_ns_even_odd_split():
+    x = O.unpack(rand_raw((2, 2048)))
+    X = O.ns_beams(x, all_bins_lut())
+    xt = np.moveaxis(x, 2, 3)
+    n = np.arange(256)
+    assert np.allclose(X[..., 0::2], np.fft.fft(xt, axis=-1), atol=1e-9)
+    assert np.allclose(X[..., 1::2], np.fft.fft(xt * np.exp(-1j * np.pi * n / 256), axis=-1), atol=1e-9)
+
+
+def test_ns_delta_and_constant():
+    x = np.zeros((1, 4, 256, 2), complex)
+    x[0, 1, 37, 0] = 1.0
+    X = O.ns_beams(x, all_bins_lut())
+    assert np.allclose(np.abs(X[0, 1, 0]), 1.0)
+    a = 3 - 2j
+    x = np.full((1, 4, 256, 2), a)
+    X = O.ns_beams(x, all_bins_lut())[0, 0, 0]
+    k = np.arange(512)
+    assert abs(X[0] - 256 * a) < 1e-9
+    assert np.allclose(X[2::2], 0, atol=1e-9)
+    odd = k[1::2]
+    assert np.allclose(X[1::2], 2 * a / (1 - np.exp(-1j * np.pi * odd / 256)), atol=1e-9)
+
+
+def test_ns_parseval():
+    x = O.unpack(rand_raw((4, 2048)))
+    X = O.ns_beams(x, all_bins_lut())
+    lhs = (np.abs(X) ** 2).sum(axis=-1)
+    rhs = 512 * (np.abs(x) ** 2).sum(axis=2)
+    assert np.allclose(lhs, rhs, rtol=1e-12)
+
+
+def test_ns_plane_wave_on_bin_and_steering_identity():
+    f, L = 700e6, 93
+    s = L * O.C0 / (512 * f * 0.3048)                  # exactly on beam L
+    a = 1.7
+    g = synth.geometric_phase(f, 0.0, s).reshape(4, 256, 2)
+    X = O.ns_beams((a * g)[None], all_bins_lut())
+    assert abs(abs(X[0, 2, 1, L]) - 256 * a) < 1e-8
+    # zero-padded bin L equals direct phasing toward s' = L c/(M f d)
+    x = O.unpack(rand_raw((1, 2048)))[0, 0, :, 0]
+    direct = sum(x[n] * cmath.exp(-2j * math.pi * f * n * 0.3048 * s / O.C0) for n in range(256))
+    assert abs(O.ns_beams(x.reshape(1, 1, 256, 1), all_bins_lut())[0, 0, 0, L] - direct) < 1e-8
+
+
+def test_alias_of_26deg_source_fig3():
+    # Sec. 3.3 / Fig. 3: a source near 26 deg has aliases, of comparable strength
+    # in one channel, between about -88 and -50 deg at the top of the band; in
+    # the frequency-summed map the source dominates and the alias is smeared.
+    t = gold("table1.json")
+    lo, hi = t["alias_smear_deg_for_26deg_source"]
+    ns = O.default_ns_sin()
+    s_src = math.sin(math.radians(26.0))
+    m_src = int(np.argmin(np.abs(ns - s_src)))
+    near = np.abs(np.arange(256) - m_src) <= 2
+    total = np.zeros(256)
+    for f in np.linspace(400e6, 800e6, 41):
+        g = synth.geometric_phase(f, 0.0, s_src).reshape(4, 256, 2)
+        P = np.abs(O.ns_beams(g[None], O.clamp_lut(f, ns))[0, 0, 0]) ** 2
+        total += P / P.max()
+        if f >= 700e6:
+            alias_deg = math.degrees(math.asin(ns[~near][np.argmax(P[~near])]))
+            assert lo - 3 <= alias_deg <= hi + 3
+            assert P[~near].max() > 0.3 * P.max()        # comparable in one channel
+    assert abs(int(np.argmax(total)) - m_src) <= 1
+    assert total[~near].max() < 0.5 * total.max()
+
+
+# --- a2 E-W beams ---------------------------------------------------------------------
+
+def test_ew_zero_angle_is_cylinder_sum():
+    X = rng.standard_normal((2, 4, 2, 256)) + 1j * rng.standard_normal((2, 4, 2, 256))
+    B = O.ew_beams(X, O.ew_weights(600e6, np.zeros(4)))
+    assert np.allclose(B, X.sum(axis=1)[:, :, None, :])
+
+
+def test_ew_dft_spaced_is_unitary():
+    f = 600e6
+    u = np.arange(4) * O.C0 / (4 * 20.0 * f)
+    X = rng.standard_normal((2, 4, 2, 256)) + 1j * rng.standard_normal((2, 4, 2, 256))
+    B = O.ew_beams(X, O.ew_weights(f, u))
+    assert np.allclose((np.abs(B) ** 2).sum(axis=2), 4 * (np.abs(X) ** 2).sum(axis=1))
+    assert np.allclose(B, np.fft.fft(X, axis=1).transpose(0, 2, 1, 3))
+
+
+# --- a3 up-channelisation -------------------------------------------------------------
+
+def test_upchan_matches_numpy_and_parseval():
+    B = rng.standard_normal((256, 2, 1, 3)) + 1j * rng.standard_normal((256, 2, 1, 3))
+    Y = O.upchannelize(B)                                  # [2, p, j, m, 128]
+    ref = np.fft.fftshift(np.fft.fft(np.moveaxis(B.reshape(2, 128, 2, 1, 3), 1, -1), axis=-1), axes=-1)
+    assert np.allclose(Y, ref, atol=1e-9)
+    assert np.allclose((np.abs(Y) ** 2).sum(-1), 128 * (np.abs(B.reshape(2, 128, 2, 1, 3)) ** 2).sum(1))
+
+
+@pytest.mark.parametrize("k", [0, 1, 5, 63, -1, -64, 40])
+def test_upchan_tone_lands_in_one_fine_channel(k):
+    tau = np.arange(128)
+    B = np.exp(2j * np.pi * k * tau / 128)[:, None, None, None]
+    Y = O.upchannelize(B)[0, 0, 0, 0]
+    qp = (k + 64) % 128                                    # shifted index, q' = 0 lowest
+    assert abs(Y[qp] - 128) < 1e-9
+    assert np.allclose(np.delete(Y, qp), 0, atol=1e-9)
+
+
+# --- a4 + a5, whole path ---------------------------------------------------------------
+
+def test_integration_parseval_invariant():
+    raw = rand_raw((768, 2048))
+    O_, st = O.beamform_channel(raw, 520e6, return_stages=True)
+    B = st["B"]                                            # [T, p, j, m]
+    e = (np.abs(B) ** 2).sum(axis=1).reshape(2, 384, 4, 256).sum(axis=1)   # [frame, j, m]
+    lhs = O_.sum(axis=1).reshape(4, 256, 2)
+    assert np.allclose(lhs, 128 * np.transpose(e, (1, 2, 0)), rtol=1e-10)
+
+
+def test_noise_mean_closed_form():
+    sigma = 2.5
+    raw = synth.noise_only([450e6], 384 * 4, seed=7, sigma=sigma)
+    out = O.beamform(raw, [450e6])
+    var = synth.quantized_noise_variance(sigma)            # per real component
+    expect = 24 * 2 * 128 * 4 * 256 * (2 * var)
+    # every output is a sum of 96 nearly independent chi^2_2 terms -> CV ~ 0.1;
+    # the mean over 65536 outputs is good to well under 1 %
+    assert abs(out.mean() / expect - 1) < 0.01
+
+
+def test_point_source_peaks_in_predicted_beam():
+    raw, f = synth.config_point_source(0)
+    out = O.beamform(raw, f)
+    # source at 20 deg N-S (bin 106.8 at 600 MHz -> pointing 171 kept at bin 106)
+    # and 0.5 deg E-W (nearest E-W beam: +0.6 deg, j = 3)
+    assert int(out.sum(axis=(1, 2)).argmax()) == 3 * 256 + 171
+
+
+def test_sample_route_matches_full_route():
+    raw, f = synth.config_point_source(3)
+    raw = raw[:, :1152]
+    full = O.beamform(raw, f)
+    picks = [(0, 939, 1), (0, 0, 0), (0, 1023, 2), (0, 300, 1)]
+    s = O.beamform_sample(raw, f, picks)
+    for i, (_, b, fr) in enumerate(picks):
+        assert np.allclose(s[i], full[b, :, fr], rtol=1e-12)
+
+
+def test_geometry_matches_table1():
+    t = gold("table1.json")
+    g = O.CHIME
+    assert g.n_input == t["n_inputs"] and g.n_sub == t["output_channels_per_input_channel"]
+    assert g.n_ew * g.n_ns == t["n_intensity_beams"] and g.pad == t["padding_factor"]
+    assert abs(g.frame * t["input_time_resolution_s"] - t["output_time_resolution_s"]) < 1e-6
+    chan = 400e6 / t["input_channels"]
+    assert abs(chan / g.n_sub - t["output_frequency_resolution_hz"]) < 0.03 * 24e3
+    assert abs(chan / g.upchan - t["upchannel_resolution_hz"]) < 0.03 * 3e3
+    raw = rand_raw((1, 384 * 2 + 100, 2048))
+    out = O.beamform(raw, [600e6])
+    assert out.shape == (1024, 16, 2)                        # trailing samples dropped
+
+
+def test_pointing_spacing_matches_fwhm_statements():
+    # Sec. 3.1: FWHM ~0.5 deg at zenith and ~2.8 deg at 10 deg elevation; the
+    # default pointings are spaced close to these widths.
+    t = gold("table1.json")
+    ns = O.default_ns_sin()
+    th = np.degrees(np.arcsin(ns))
+    zen = np.diff(th)[127]
+    low_el = 90.0 - t["low_elevation_deg"]
+    k = int(np.searchsorted(th, low_el)) - 1          # interval holding 80 deg
+    assert abs(zen - t["zenith_fwhm_deg_approx"]) < 0.1
+    assert abs(np.diff(th)[k] - t["low_elevation_fwhm_deg_approx"]) < 0.5
+
+
+# --- brute force on a tiny geometry -----------------------------------------------------
+
+TINY = O.Geometry(n_cyl=2, n_feed=4, n_pol=2, pad=2, n_ew=2, upchan=4, f_ds=2, t_ds=2,
+                  feed_spacing_m=0.3048, cyl_spacing_m=20.0)
+
+
+def brute_force(raw, freq, ns_sin, ew_sin, g):
+    """Literal loops over the definition, one term at a time."""
+    M, U = g.n_bins, g.upchan
+    T = raw.shape[0]
+    nfr = T // g.frame
+    lut = nearest_beam_bins(freq, ns_sin, g)
+    out = np.zeros((g.n_ew * g.n_ns, g.n_sub, nfr))
+    for fr in range(nfr):
+        for j in range(g.n_ew):
+            for m in range(g.n_ns):
+                for blk in range(g.t_ds):
+                    for p in range(g.n_pol):
+                        beam = []
+                        for tau in range(U):
+                            t = fr * g.frame + blk * U + tau
+                            acc = 0j
+                            for c in range(g.n_cyl):
+                                xc = 0j
+                                for n in range(g.n_feed):
+                                    byte = int(raw[t, (c * g.n_feed + n) * g.n_pol + p])
+                                    v = complex((byte >> 4) - 8, (byte & 15) - 8)
+                                    xc += v * cmath.exp(-2j * math.pi * n * lut[m] / M)
+                                acc += xc * cmath.exp(-2j * math.pi * freq * c * g.cyl_spacing_m * ew_sin[j] / O.C0)
+                            beam.append(acc)
+                        for q in range(U):
+                            yq = sum(beam[tau] * cmath.exp(-2j * math.pi * q * tau / U) for tau in range(U))
+                            qp = (q + U // 2) % U
+                            out[j * g.n_ns + m, qp // g.f_ds, fr] += abs(yq) ** 2
+    return out
+
+
+@pytest.mark.parametrize("freq", [450e6, 780e6])
+def test_brute_force_tiny_geometry(freq):
+    g = TINY
+    T = g.frame * 2 + 3
+    raw = rand_raw((T, g.n_input), clip=8 - 1)
+    raw[0, 0] = 0x00                                   # the -8 code decodes too
+    ns = np.array([-0.9, -0.2, 0.3, 0.95])
+    ew = np.sin(np.radians([-0.4, 0.5]))
+    ref = brute_force(raw, freq, ns, ew, g)
+    got = O.beamform_channel(raw, freq, ns, ew, g)
+    assert got.shape == ref.shape
+    assert np.allclose(got, ref, rtol=1e-10, atol=1e-9)
