@@ -1,0 +1,176 @@
+/*
+ * chimebf.h -- C ABI of the GB300 CHIME/FRB fan-beam library (arXiv 1702.04728).
+ *
+ * One coarse frequency channel carries 4+4-bit complex voltages from 2048
+ * inputs (4 cylinders x 256 feeds x 2 polarisations; Sec. 2, Table 1).  The
+ * library turns them into Stokes-I intensity for 1024 beams (256 N-S x 4 E-W)
+ * at 16 sub-channels x one frame per 384 samples (Sec. 3, Table 1):
+ *
+ *   1. N-S beams: 2x zero-padded 512-point FFT of each 256-feed line, kept at
+ *      the 256 bins of the clamp table of Eq. (1) (Sec. 3.1);
+ *   2. 4 E-W beams by exact phasing across the cylinders (Sec. 3);
+ *   3. up-channelisation by a 128-point FFT over time (Sec. 3.2);
+ *   4. |.|^2 summed over polarisation (Sec. 3);
+ *   5. sums over 8 fine channels x 3 blocks (24 kHz, 0.983 ms; Sec. 3, Table 1).
+ *
+ * Data layouts (all row-major, C order):
+ *   input  uint8 [n_chan][n_samples][2048]; byte (cyl*256 + feed)*2 + pol;
+ *          high nibble = real + 8, low nibble = imaginary + 8.
+ *   output float [1024][16*n_chan][n_frames]; beam = 256*ew + ns,
+ *          sub-channel = 16*chan + s with s = 0 the lowest frequency.
+ *
+ * Error behaviour: every call returns an int status; negative values are
+ * errors, no call aborts the process, and bf_last_error() gives a message for
+ * the calling thread's last failure.
+ */
+#ifndef CHIMEBF_H
+#define CHIMEBF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define BF_OK          0
+#define BF_PENDING     1   /* bf_poll: not finished within the timeout              */
+#define BF_EQUEUED     2   /* bf_submit: accepted, waiting for memory or a slot     */
+#define BF_EINVAL     -1   /* bad argument or unsupported geometry                  */
+#define BF_ENOMEM     -2   /* request larger than the plan's whole memory budget    */
+#define BF_ECUDA      -3   /* a CUDA call failed (message in bf_last_error)         */
+#define BF_ETIMEDOUT  -4   /* a bounded device-side wait expired                    */
+#define BF_ENOTICKET  -5   /* unknown, already collected or cancelled ticket        */
+#define BF_ESHUTDOWN  -6   /* plan is being destroyed                               */
+
+/* N-S transform forms (bf_config.form) */
+#define BF_FP32_FFT    0   /* FP32 zero-padded FFT on the CUDA cores                */
+#define BF_TC_DFT256   1   /* tensor-core DFT GEMM over the 256 clamped rows        */
+#define BF_TC_DFT512   2   /* tensor-core DFT GEMM over all 512 padded rows         */
+
+/* execution modes (bf_config.mode) */
+#define BF_MODE_DIRECT   0 /* bf_submit launches at once on cuda_stream             */
+#define BF_MODE_SERVING  1 /* a plan thread batches queued requests into launches   */
+
+/* request flags */
+#define BF_END_OF_STREAM 1 /* drop the stream's leftover samples after this request */
+
+typedef struct bf_plan_s* bf_plan_t;
+
+/*
+ * Plan configuration.  Geometry follows Sec. 1 (4 cylinders, 256 feeds at
+ * 0.3048 m, dual polarisation), Sec. 3.1 (padding P = 2), Sec. 3 (4 E-W
+ * beams) and Sec. 3.2 / Table 1 (128-point up-channelisation, 16 output
+ * sub-channels, 0.983 ms = 3 blocks of 128 samples).  The kernels are built
+ * for exactly this geometry; other integer values return BF_EINVAL.  The
+ * spacings and pointings are free (Sec. 3.1: the N-S tiling is tunable).
+ */
+typedef struct {
+    int n_cyl;              /* 4   */
+    int n_feed;             /* 256 */
+    int n_pol;              /* 2   */
+    int pad;                /* 2   */
+    int n_ew;               /* 4   */
+    int upchan;             /* 128 */
+    int f_ds;               /* 8   */
+    int t_ds;               /* 3   */
+    double feed_spacing_m;  /* N-S feed spacing d, 0.3048                         */
+    double cyl_spacing_m;   /* E-W cylinder spacing, 20.0                         */
+    double dt_s;            /* sample cadence, 2.56e-6 (bookkeeping only)         */
+    const double* ns_sin;   /* host [n_feed] sin(theta_m) of the N-S pointings, or
+                               NULL for (m - 127.5)/128; copied by bf_plan        */
+    const double* ew_sin;   /* host [n_ew] sin of the E-W beam angles, or NULL for
+                               sin({-0.6, -0.2, 0.2, 0.6} deg); copied            */
+    int form;               /* BF_FP32_FFT | BF_TC_DFT256 | BF_TC_DFT512          */
+    int mode;               /* BF_MODE_DIRECT | BF_MODE_SERVING                   */
+    size_t mem_budget;      /* serving admission budget in bytes (0 = unlimited)  */
+    int max_streams;        /* distinct stream_ids held at once (0 = 1024)        */
+    void* cuda_stream;      /* cudaStream_t for the launches, or NULL: the plan
+                               creates its own non-blocking stream                */
+    int device;             /* CUDA device ordinal, or -1 for the current device  */
+} bf_config;
+
+/* Fill *cfg with the CHIME defaults above.  Returns BF_OK or BF_EINVAL. */
+int bf_config_default(bf_config* cfg);
+
+/*
+ * Create a plan: validates cfg, precomputes in FP64 the twiddle tables and
+ * allocates device memory for per-frequency tables (clamp table of Eq. (1)
+ * and E-W phases, filled lazily per channel frequency) and stream carry state.
+ * On success *out owns everything and must be released with bf_destroy.
+ */
+int bf_plan(const bf_config* cfg, bf_plan_t* out);
+
+/*
+ * One request: n_samples new samples of n_chan channels of stream stream_id.
+ * vin   device pointer, uint8 [n_chan][n_samples][2048], caller-owned.
+ * out   device pointer, float [1024][16*n_chan][n_frames_out], caller-owned,
+ *       n_frames_out = floor((carry + n_samples) / 384) where carry (< 384) is
+ *       the number of samples the stream left over from earlier requests.
+ * chan_freq_hz  host [n_chan] coarse-channel centre frequencies (they select
+ *       the clamp table of Eq. (1) and the E-W phases); a stream keeps the
+ *       frequencies of its first request.
+ * Both buffers must stay valid until bf_poll returns BF_OK for the ticket.
+ */
+typedef struct {
+    uint64_t stream_id;
+    int n_chan;
+    const double* chan_freq_hz;
+    int64_t n_samples;
+    const uint8_t* vin;
+    float* out;
+    int flags;              /* 0 or BF_END_OF_STREAM */
+} bf_request;
+
+/* Frames a request will produce given the stream's current carry (host-side). */
+int bf_frames_out(bf_plan_t p, uint64_t stream_id, int64_t n_samples, int64_t* n_frames_out);
+
+/*
+ * Submit a request.  DIRECT mode: the work is enqueued on the plan's stream
+ * before returning (BF_OK).  SERVING mode: the request is queued (BF_OK if it
+ * was admitted at once, BF_EQUEUED if it waits for memory); the plan thread
+ * batches admitted requests of different streams into one launch.  *ticket
+ * identifies the request for bf_poll.  Requests of one stream run in order.
+ */
+int bf_submit(bf_plan_t p, const bf_request* r, uint64_t* ticket);
+
+/*
+ * Wait up to timeout_us microseconds (0 = just test, <0 = forever) for a
+ * ticket.  BF_OK: output written, *n_frames_out set, ticket released.
+ * BF_PENDING: still running.  Negative: error (the ticket is released).
+ */
+int bf_poll(bf_plan_t p, uint64_t ticket, int64_t timeout_us, int64_t* n_frames_out);
+
+/* Drain outstanding work, free all plan-owned memory and the plan thread. */
+int bf_destroy(bf_plan_t p);
+
+/* Message for the calling thread's last error ("" if none). */
+const char* bf_last_error(void);
+
+/* ---- inspection entry points (used by the parity tests) ------------------ */
+
+/* Host-only: the clamp table (Eq. 1) [n_feed] and E-W weights [n_ew][n_cyl]
+ * complex (interleaved re, im; FP32 rounding of FP64 values) that a plan with
+ * configuration cfg uses for one frequency.  Needs no GPU; either output may
+ * be NULL. */
+int bf_debug_tables(const bf_config* cfg, double freq_hz, int32_t* lut_out, float* ew_out);
+
+/* Device unpack of n bytes into 2n floats (re, im), with the same device
+ * code the fused kernel uses.  d_in, d_out device pointers. */
+int bf_debug_unpack(bf_plan_t p, const uint8_t* d_in, float* d_out, int64_t n);
+
+/* Stages 1+2 for one channel: complex beams float2 [T][pol][ew][ns] from
+ * uint8 [T][2048], computed by the fused kernel's N-S/E-W device code. */
+int bf_debug_beams(bf_plan_t p, double freq_hz, const uint8_t* d_vin, int64_t n_samples, float* d_out);
+
+/* Stages 1-3 for one channel: up-channelised complex voltages float2
+ * [block][pol][ew][ns][q'] (q' fftshifted) for n_samples a multiple of 384,
+ * computed by the fused kernel with detection replaced by a dump. */
+int bf_debug_upchan(bf_plan_t p, double freq_hz, const uint8_t* d_vin, int64_t n_samples, float* d_out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CHIMEBF_H */

@@ -1,0 +1,245 @@
+"""ctypes binding of the C ABI in ``include/chimebf.h`` (argument marshalling only).
+
+Every step of the beamformer runs in ``_lib/libchimebf.so``; this module only
+packs arguments.  Torch tensors are accepted for device buffers and streams
+(``data_ptr()`` / ``cuda_stream``).  Importing it does not load the library;
+the first call does, and raises if the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libchimebf.so")
+
+BF_OK, BF_PENDING, BF_EQUEUED = 0, 1, 2
+BF_EINVAL, BF_ENOMEM, BF_ECUDA, BF_ETIMEDOUT, BF_ENOTICKET, BF_ESHUTDOWN = -1, -2, -3, -4, -5, -6
+BF_FP32_FFT, BF_TC_DFT256, BF_TC_DFT512 = 0, 1, 2
+BF_MODE_DIRECT, BF_MODE_SERVING = 0, 1
+BF_END_OF_STREAM = 1
+
+N_BEAMS, N_SUB, FRAME, N_INPUT = 1024, 16, 384, 2048
+
+SYMBOLS = ["bf_config_default", "bf_plan", "bf_frames_out", "bf_submit", "bf_poll", "bf_destroy",
+           "bf_last_error", "bf_debug_tables", "bf_debug_unpack", "bf_debug_beams", "bf_debug_upchan"]
+
+
+class BfError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"chimebf error {code}: {msg}")
+        self.code = code
+
+
+class bf_config(ctypes.Structure):
+    _fields_ = [("n_cyl", ctypes.c_int), ("n_feed", ctypes.c_int), ("n_pol", ctypes.c_int),
+                ("pad", ctypes.c_int), ("n_ew", ctypes.c_int), ("upchan", ctypes.c_int),
+                ("f_ds", ctypes.c_int), ("t_ds", ctypes.c_int),
+                ("feed_spacing_m", ctypes.c_double), ("cyl_spacing_m", ctypes.c_double),
+                ("dt_s", ctypes.c_double),
+                ("ns_sin", ctypes.POINTER(ctypes.c_double)), ("ew_sin", ctypes.POINTER(ctypes.c_double)),
+                ("form", ctypes.c_int), ("mode", ctypes.c_int), ("mem_budget", ctypes.c_size_t),
+                ("max_streams", ctypes.c_int), ("cuda_stream", ctypes.c_void_p), ("device", ctypes.c_int)]
+
+
+class bf_request(ctypes.Structure):
+    _fields_ = [("stream_id", ctypes.c_uint64), ("n_chan", ctypes.c_int),
+                ("chan_freq_hz", ctypes.POINTER(ctypes.c_double)), ("n_samples", ctypes.c_int64),
+                ("vin", ctypes.c_void_p), ("out", ctypes.c_void_p), ("flags", ctypes.c_int)]
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load ``libchimebf.so`` (once); raise if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
+                               "(the beamformer has no CPU fallback)")
+        L = ctypes.CDLL(LIB_PATH)
+        P, I, I64, U64, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
+        L.bf_config_default.argtypes = [ctypes.POINTER(bf_config)]
+        L.bf_plan.argtypes = [ctypes.POINTER(bf_config), ctypes.POINTER(P)]
+        L.bf_frames_out.argtypes = [P, U64, I64, ctypes.POINTER(I64)]
+        L.bf_submit.argtypes = [P, ctypes.POINTER(bf_request), ctypes.POINTER(U64)]
+        L.bf_poll.argtypes = [P, U64, I64, ctypes.POINTER(I64)]
+        L.bf_destroy.argtypes = [P]
+        L.bf_last_error.argtypes = []
+        L.bf_last_error.restype = ctypes.c_char_p
+        L.bf_debug_tables.argtypes = [ctypes.POINTER(bf_config), D, ctypes.POINTER(ctypes.c_int32),
+                                      ctypes.POINTER(ctypes.c_float)]
+        L.bf_debug_unpack.argtypes = [P, P, P, I64]
+        L.bf_debug_beams.argtypes = [P, D, P, I64, P]
+        L.bf_debug_upchan.argtypes = [P, D, P, I64, P]
+        for name in SYMBOLS:
+            getattr(L, name).restype = ctypes.c_char_p if name == "bf_last_error" else I
+        _lib = L
+    return _lib
+
+
+def bf_last_error() -> str:
+    return lib().bf_last_error().decode()
+
+
+def _check(rc: int) -> int:
+    if rc < 0:
+        raise BfError(rc, bf_last_error())
+    return rc
+
+
+def _ptr(x) -> Optional[int]:
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def _dbl_array(vals):
+    if vals is None:
+        return None, None
+    arr = (ctypes.c_double * len(vals))(*[float(v) for v in vals])
+    return ctypes.cast(arr, ctypes.POINTER(ctypes.c_double)), arr
+
+
+CUDA_STREAM_LEGACY = 1      # cudaStreamLegacy: the legacy default stream
+
+
+def stream_handle(s) -> Optional[int]:
+    """cudaStream_t for a torch stream or an int; the legacy default stream
+    (torch handle 0) maps to cudaStreamLegacy, since NULL asks the plan to
+    create a stream of its own."""
+    if s is None:
+        return None
+    h = getattr(s, "cuda_stream", s)
+    return CUDA_STREAM_LEGACY if h == 0 else h
+
+
+def bf_config_default(**kw) -> bf_config:
+    cfg = bf_config()
+    _check(lib().bf_config_default(ctypes.byref(cfg)))
+    keep = []
+    for k, v in kw.items():
+        if k in ("ns_sin", "ew_sin"):
+            ptr, arr = _dbl_array(v)
+            keep.append(arr)
+            setattr(cfg, k, ptr)
+        elif k == "cuda_stream":
+            cfg.cuda_stream = stream_handle(v)
+        else:
+            setattr(cfg, k, v)
+    cfg._keep = keep                      # arrays must outlive bf_plan's copy
+    return cfg
+
+
+def bf_plan(cfg: bf_config) -> int:
+    h = ctypes.c_void_p()
+    _check(lib().bf_plan(ctypes.byref(cfg), ctypes.byref(h)))
+    return h.value
+
+
+def bf_frames_out(plan: int, stream_id: int, n_samples: int) -> int:
+    nf = ctypes.c_int64()
+    _check(lib().bf_frames_out(plan, stream_id, n_samples, ctypes.byref(nf)))
+    return nf.value
+
+
+def bf_submit(plan: int, stream_id: int, freqs: Sequence[float], n_samples: int, vin, out,
+              flags: int = 0):
+    """Returns (status, ticket); status is BF_OK or BF_EQUEUED."""
+    fptr, farr = _dbl_array(list(freqs))
+    req = bf_request(stream_id, len(freqs), fptr, n_samples, _ptr(vin), _ptr(out), flags)
+    t = ctypes.c_uint64()
+    rc = _check(lib().bf_submit(plan, ctypes.byref(req), ctypes.byref(t)))
+    del farr
+    return rc, t.value
+
+
+def bf_poll(plan: int, ticket: int, timeout_us: int = -1):
+    """Returns (status, n_frames_out); status BF_OK or BF_PENDING."""
+    nf = ctypes.c_int64()
+    rc = _check(lib().bf_poll(plan, ticket, timeout_us, ctypes.byref(nf)))
+    return rc, nf.value
+
+
+def bf_destroy(plan: int) -> None:
+    _check(lib().bf_destroy(plan))
+
+
+def bf_debug_tables(freq_hz: float, cfg: Optional[bf_config] = None):
+    import numpy as np
+    cfg = cfg or bf_config_default()
+    lut = (ctypes.c_int32 * 256)()
+    ew = (ctypes.c_float * 32)()
+    _check(lib().bf_debug_tables(ctypes.byref(cfg), float(freq_hz), lut, ew))
+    w = np.frombuffer(ew, dtype=np.float32).reshape(4, 4, 2)
+    return np.frombuffer(lut, dtype=np.int32).copy(), (w[..., 0] + 1j * w[..., 1]).astype(np.complex64)
+
+
+def bf_debug_unpack(plan: int, d_in, d_out, n: int) -> None:
+    _check(lib().bf_debug_unpack(plan, _ptr(d_in), _ptr(d_out), n))
+
+
+def bf_debug_beams(plan: int, freq_hz: float, d_vin, n_samples: int, d_out) -> None:
+    _check(lib().bf_debug_beams(plan, float(freq_hz), _ptr(d_vin), n_samples, _ptr(d_out)))
+
+
+def bf_debug_upchan(plan: int, freq_hz: float, d_vin, n_samples: int, d_out) -> None:
+    _check(lib().bf_debug_upchan(plan, float(freq_hz), _ptr(d_vin), n_samples, _ptr(d_out)))
+
+
+# ---- convenience over torch device memory (allocation and marshalling only) ----
+
+class Plan:
+    """Owns a bf_plan_t.  ``run`` submits one request and waits for it."""
+
+    def __init__(self, mode: int = BF_MODE_DIRECT, stream="current", **cfg_kw):
+        """stream: a torch stream or cudaStream_t; "current" (default) takes
+        torch's current stream, None lets the plan create its own."""
+        if isinstance(stream, str) and stream == "current":
+            import torch
+            stream = torch.cuda.current_stream()
+        self.cfg = bf_config_default(mode=mode, cuda_stream=stream, **cfg_kw)
+        self.handle = bf_plan(self.cfg)
+
+    def frames_out(self, stream_id: int, n_samples: int) -> int:
+        return bf_frames_out(self.handle, stream_id, n_samples)
+
+    def submit(self, vin, freqs, out, stream_id: int = 0, flags: int = 0, n_samples: Optional[int] = None):
+        if n_samples is None:
+            n_samples = vin.shape[-2]
+        return bf_submit(self.handle, stream_id, freqs, n_samples, vin, out, flags)
+
+    def poll(self, ticket: int, timeout_us: int = -1):
+        return bf_poll(self.handle, ticket, timeout_us)
+
+    def run(self, vin, freqs, stream_id: int = 0, flags: int = BF_END_OF_STREAM):
+        """vin: torch.uint8 CUDA tensor [n_chan, T, 2048] -> float32 [1024, 16 n_chan, n_frames]."""
+        import torch
+        n_chan, T = int(vin.shape[0]), int(vin.shape[1])
+        nf = self.frames_out(stream_id, T)
+        out = torch.empty((N_BEAMS, N_SUB * n_chan, nf), dtype=torch.float32, device=vin.device)
+        _, t = self.submit(vin, freqs, out, stream_id, flags, T)
+        rc, got = self.poll(t)
+        assert got == nf
+        return out
+
+    def close(self) -> None:
+        if self.handle:
+            bf_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,62 @@
+// Internal interface between the host runtime (runtime.cpp) and the CUDA
+// kernels (fused_fp32.cu).  Not part of the public C ABI.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace chimebf {
+
+// Geometry the kernels are built for (Sec. 1, Sec. 2, Sec. 3, Table 1).
+constexpr int kCyl = 4;          // cylinders
+constexpr int kFeed = 256;       // feeds per cylinder (N)
+constexpr int kPol = 2;          // polarisations
+constexpr int kBins = 512;       // zero-padded N-S FFT length (N P, P = 2)
+constexpr int kNs = 256;         // N-S beams kept by the clamp
+constexpr int kEw = 4;           // E-W beams
+constexpr int kUp = 128;         // up-channelisation FFT length
+constexpr int kFds = 8;          // fine channels per output sub-channel
+constexpr int kTds = 3;          // 128-sample blocks per output frame
+constexpr int kSub = kUp / kFds; // 16 sub-channels
+constexpr int kFrame = kUp * kTds;   // 384 samples per frame
+constexpr int kInput = kCyl * kFeed * kPol;   // 2048 bytes per time sample
+constexpr int kBeams = kEw * kNs;    // 1024 intensity beams
+
+// Segments per launch (kernel-parameter space holds the descriptors).
+constexpr int kMaxSegs = 160;
+
+// One (request, channel): a frame stream made of `carry_rows` leftover rows
+// followed by the request's new rows.
+struct Seg {
+    const uint8_t* vin;      // row 0 of this channel's new samples [n][2048]
+    const uint8_t* carry;    // leftover rows [carry_rows][2048] (may be null)
+    float* out;              // &out[beam 0][sub 16*chan][frame 0] of the request
+    long long beam_stride;   // elements between beams  (16 * n_chan * n_frames)
+    int sub_stride;          // elements between sub-channels (n_frames)
+    int carry_rows;          // 0..383
+    int n_frames;            // frames of this segment
+    int table;               // row of the per-frequency tables
+    int item_begin;          // first work item; 4 items (E-W beams) per frame
+    int pad_;
+};
+
+struct Batch {
+    int n_segs;
+    int n_items;
+    const int16_t* lut;      // [n_tables][256]   clamp table, Eq. (1)
+    const float2* ew;        // [n_tables][4 ew][4 cyl] E-W phases
+    const float2* tw512;     // [512] exp(-2 pi i e / 512)
+    const float2* tw128;     // [128] exp(-2 pi i e / 128)
+    float2* dump;            // debug: up-channelised voltages instead of detection
+    Seg segs[kMaxSegs];
+};
+
+// Launches of the CUDA code; each returns the launch status.
+cudaError_t fused_fp32_launch(const Batch& b, int grid, cudaStream_t s);
+cudaError_t fused_fp32_dump_launch(const Batch& b, int grid, cudaStream_t s);
+cudaError_t debug_beams_launch(const uint8_t* vin, long long n_samples, const int16_t* lut,
+                               const float2* ew, const float2* tw512, float2* out, cudaStream_t s);
+cudaError_t debug_unpack_launch(const uint8_t* in, float* out, long long n, cudaStream_t s);
+int fused_fp32_max_grid(int device);   // CTAs that fit at once (1 per SM)
+
+}  // namespace chimebf

@@ -1,0 +1,687 @@
+// Host runtime behind the C ABI of include/chimebf.h.
+//
+// A plan owns: FP64-derived device tables (clamp table of Eq. 1 and E-W
+// phases per channel frequency, FFT twiddles), per-stream carry buffers (the
+// < 384 samples left over between requests of one stream), and in SERVING
+// mode a thread that batches queued requests of different streams into one
+// launch of the fused kernel (continuous batching: requests that arrive while
+// a batch runs join the next one, admitted against a memory budget).
+#include "../../include/chimebf.h"
+#include "bf_internal.h"
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+using namespace chimebf;
+
+namespace {
+
+constexpr double kC0 = 299792458.0;
+constexpr double kPi = 3.14159265358979323846;
+constexpr int kTableCap = 4096;
+constexpr int kMaxInflight = 4;
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+    g_err = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+    return fail(BF_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                   \
+    do {                                           \
+        cudaError_t e_ = (call);                   \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+    } while (0)
+
+struct StreamState {
+    int n_chan = 0;
+    std::vector<int> tables;        // per channel
+    uint8_t* carry = nullptr;       // device [n_chan][kFrame - 1][2048]
+    int carry_rows = 0;
+    size_t carry_bytes = 0;
+};
+
+enum TicketState { T_QUEUED, T_INFLIGHT, T_DONE, T_ERROR };
+
+struct Ticket {
+    TicketState state = T_QUEUED;
+    int64_t n_frames = 0;
+    int err = 0;
+    std::string msg;
+    size_t bytes = 0;               // admission accounting
+    uint64_t batch = 0;
+};
+
+struct Job {
+    uint64_t ticket;
+    bf_request req;
+    std::vector<double> freqs;
+};
+
+struct InflightBatch {
+    uint64_t id;
+    cudaEvent_t ev;
+    std::vector<uint64_t> tickets;
+    size_t bytes;
+};
+
+}  // namespace
+
+struct bf_plan_s {
+    bf_config cfg{};
+    std::vector<double> ns_sin, ew_sin;
+    int device = 0;
+    int grid = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+
+    int16_t* d_lut = nullptr;
+    float2* d_ew = nullptr;
+    float2* d_tw512 = nullptr;
+    float2* d_tw128 = nullptr;
+    std::map<uint64_t, int> table_of_freq;   // key: bit pattern of the double
+
+    std::mutex mu;
+    std::condition_variable cv;
+    std::unordered_map<uint64_t, StreamState> streams;
+    std::unordered_map<uint64_t, Ticket> tickets;
+    uint64_t next_ticket = 1;
+    uint64_t next_batch = 1;
+    std::deque<Job> queue;
+    std::deque<InflightBatch> inflight;
+    std::vector<cudaEvent_t> event_pool;
+    size_t mem_in_use = 0;
+    bool stop = false;
+    std::thread worker;
+};
+
+namespace {
+
+// Copy the N-S and E-W pointings of cfg (or the defaults) into p.
+int fill_pointings(bf_plan_s* p, const bf_config* cfg) {
+    for (int m = 0; m < kNs; ++m) {
+        p->ns_sin[m] = cfg->ns_sin ? cfg->ns_sin[m] : (m - 127.5) / 128.0;
+        if (!std::isfinite(p->ns_sin[m])) return fail(BF_EINVAL, "non-finite N-S pointing");
+    }
+    static const double deg[4] = {-0.6, -0.2, 0.2, 0.6};
+    for (int j = 0; j < kEw; ++j) {
+        p->ew_sin[j] = cfg->ew_sin ? cfg->ew_sin[j] : std::sin(deg[j] * kPi / 180.0);
+        if (!std::isfinite(p->ew_sin[j])) return fail(BF_EINVAL, "non-finite E-W pointing");
+    }
+    return BF_OK;
+}
+
+// ---- tables -------------------------------------------------------------------
+
+// Eq. (1): L = floor(N P f d sin(theta) / c + 0.5), product left to right in
+// FP64, wrapped into [0, N P) (the wrap is the spatial aliasing of Sec. 3.3).
+void clamp_table(const bf_plan_s* p, double f, int32_t* lut) {
+    const double np = double(p->cfg.n_feed * p->cfg.pad);
+    for (int m = 0; m < kNs; ++m) {
+        const double arg = (((np * f) * p->cfg.feed_spacing_m) * p->ns_sin[m]) / kC0;
+        long long L = (long long)std::floor(arg + 0.5);
+        L %= kBins;
+        if (L < 0) L += kBins;
+        lut[m] = (int32_t)L;
+    }
+}
+
+// E-W phasing (Sec. 3): cylinder c at c * D, beam j toward u_j:
+// w[j][c] = exp(-2 pi i f c D u_j / c).
+void ew_table(const bf_plan_s* p, double f, float* ew) {
+    for (int j = 0; j < kEw; ++j)
+        for (int c = 0; c < kCyl; ++c) {
+            const double cyc = (((f * c) * p->cfg.cyl_spacing_m) * p->ew_sin[j]) / kC0;
+            const double fr = cyc - std::floor(cyc);
+            ew[2 * (j * kCyl + c)] = (float)std::cos(-2.0 * kPi * fr);
+            ew[2 * (j * kCyl + c) + 1] = (float)std::sin(-2.0 * kPi * fr);
+        }
+}
+
+uint64_t freq_key(double f) {
+    uint64_t k;
+    std::memcpy(&k, &f, sizeof k);
+    return k;
+}
+
+// Index of the device table row for frequency f (uploaded on first use).
+int table_for(bf_plan_s* p, double f, int* idx) {
+    auto it = p->table_of_freq.find(freq_key(f));
+    if (it != p->table_of_freq.end()) {
+        *idx = it->second;
+        return BF_OK;
+    }
+    const int n = (int)p->table_of_freq.size();
+    if (n >= kTableCap) return fail(BF_ENOMEM, "too many distinct channel frequencies in one plan");
+    int32_t lut[kNs];
+    int16_t lut16[kNs];
+    float ew[2 * kEw * kCyl];
+    clamp_table(p, f, lut);
+    for (int m = 0; m < kNs; ++m) lut16[m] = (int16_t)lut[m];
+    ew_table(p, f, ew);
+    CK(cudaMemcpy(p->d_lut + (size_t)n * kNs, lut16, sizeof lut16, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(p->d_ew + (size_t)n * kEw * kCyl, ew, sizeof ew, cudaMemcpyHostToDevice));
+    p->table_of_freq[freq_key(f)] = n;
+    *idx = n;
+    return BF_OK;
+}
+
+Batch make_batch(const bf_plan_s* p) {
+    Batch b;
+    std::memset(&b, 0, sizeof b);
+    b.lut = p->d_lut;
+    b.ew = p->d_ew;
+    b.tw512 = p->d_tw512;
+    b.tw128 = p->d_tw128;
+    return b;
+}
+
+int validate_request(const bf_request* r) {
+    if (!r) return fail(BF_EINVAL, "null request");
+    if (r->n_chan <= 0 || r->n_chan > 4096) return fail(BF_EINVAL, "n_chan out of range");
+    if (r->n_samples < 0) return fail(BF_EINVAL, "negative n_samples");
+    if (!r->chan_freq_hz) return fail(BF_EINVAL, "null chan_freq_hz");
+    for (int c = 0; c < r->n_chan; ++c)
+        if (!(r->chan_freq_hz[c] > 0.0) || !std::isfinite(r->chan_freq_hz[c]))
+            return fail(BF_EINVAL, "channel frequency must be positive and finite");
+    if (r->n_samples > 0 && !r->vin) return fail(BF_EINVAL, "null vin");
+    if (((uintptr_t)r->vin & 15) != 0) return fail(BF_EINVAL, "vin must be 16-byte aligned");
+    if (r->flags & ~BF_END_OF_STREAM) return fail(BF_EINVAL, "unknown flags");
+    return BF_OK;
+}
+
+int64_t frames_for(const bf_plan_s* p, const bf_request* r, int carry_rows) {
+    (void)p;
+    return (carry_rows + r->n_samples) / kFrame;
+}
+
+size_t request_bytes(const bf_request* r, int64_t nf, bool new_stream) {
+    size_t b = (size_t)r->n_chan * (size_t)r->n_samples * kInput;
+    b += (size_t)kBeams * kSub * r->n_chan * (size_t)nf * sizeof(float);
+    if (new_stream) b += (size_t)r->n_chan * (kFrame - 1) * kInput;
+    return b;
+}
+
+// Stream state for a request (created on first use).  Caller holds the lock.
+int stream_for(bf_plan_s* p, const bf_request* r, StreamState** out) {
+    auto it = p->streams.find(r->stream_id);
+    if (it != p->streams.end()) {
+        if (it->second.n_chan != r->n_chan) return fail(BF_EINVAL, "stream changed its channel count");
+        *out = &it->second;
+        return BF_OK;
+    }
+    const int cap = p->cfg.max_streams > 0 ? p->cfg.max_streams : 1024;
+    if ((int)p->streams.size() >= cap) return fail(BF_ENOMEM, "too many open streams");
+    StreamState s;
+    s.n_chan = r->n_chan;
+    s.tables.resize(r->n_chan);
+    for (int c = 0; c < r->n_chan; ++c) {
+        int rc = table_for(p, r->chan_freq_hz[c], &s.tables[c]);
+        if (rc) return rc;
+    }
+    s.carry_bytes = (size_t)r->n_chan * (kFrame - 1) * kInput;
+    CK(cudaMalloc(&s.carry, s.carry_bytes));
+    auto res = p->streams.emplace(r->stream_id, std::move(s));
+    *out = &res.first->second;
+    return BF_OK;
+}
+
+// Enqueue one batch of jobs (one job per stream at most) on the plan stream:
+// the fused kernel over all their frames, then the carry updates, then an
+// event.  Caller holds the lock.  Returns BF_OK or an error.
+int launch_jobs(bf_plan_s* p, std::vector<Job>& jobs, size_t bytes) {
+    struct Carry {
+        StreamState* st;
+        const uint8_t* vin;
+        int64_t n;
+        int64_t nf;
+        int old_rows;
+        int new_rows;
+        int n_chan;
+        bool drop;
+        uint64_t sid;
+    };
+    std::vector<Carry> carries;
+    std::vector<Batch> batches;
+    Batch b = make_batch(p);
+    for (auto& jb : jobs) {
+        StreamState* st = nullptr;
+        int rc = stream_for(p, &jb.req, &st);
+        if (rc) return rc;
+        const int64_t nf = frames_for(p, &jb.req, st->carry_rows);
+        const int new_rows = (int)((st->carry_rows + jb.req.n_samples) % kFrame);
+        p->tickets[jb.ticket].n_frames = nf;
+        for (int c = 0; c < jb.req.n_chan && nf > 0; ++c) {
+            if (b.n_segs == kMaxSegs) {
+                batches.push_back(b);
+                b = make_batch(p);
+            }
+            Seg& s = b.segs[b.n_segs++];
+            s.vin = jb.req.vin + (size_t)c * jb.req.n_samples * kInput;
+            s.carry = st->carry + (size_t)c * (kFrame - 1) * kInput;
+            s.out = jb.req.out + (size_t)kSub * c * nf;
+            s.beam_stride = (long long)kSub * jb.req.n_chan * nf;
+            s.sub_stride = (int)nf;
+            s.carry_rows = st->carry_rows;
+            s.n_frames = (int)nf;
+            s.table = st->tables[c];
+            s.item_begin = b.n_items;
+            b.n_items += (int)nf * kEw;
+        }
+        carries.push_back({st, jb.req.vin, jb.req.n_samples, nf, st->carry_rows, new_rows, jb.req.n_chan,
+                           (jb.req.flags & BF_END_OF_STREAM) != 0, jb.req.stream_id});
+        st->carry_rows = new_rows;      // host view advances at launch time
+    }
+    if (b.n_segs) batches.push_back(b);
+    for (auto& bb : batches) {
+        cudaError_t e = fused_fp32_launch(bb, std::min(p->grid, bb.n_items), p->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "fused kernel launch");
+    }
+    for (auto& c : carries) {
+        if (c.drop) continue;
+        int64_t src_row, dst_row, rows;
+        if (c.nf > 0) {
+            src_row = c.n - c.new_rows;
+            dst_row = 0;
+            rows = c.new_rows;
+        } else {
+            src_row = 0;
+            dst_row = c.old_rows;
+            rows = c.n;
+        }
+        if (rows > 0) {
+            CK(cudaMemcpy2DAsync(c.st->carry + dst_row * kInput, (size_t)(kFrame - 1) * kInput,
+                                 c.vin + src_row * kInput, (size_t)c.n * kInput, (size_t)rows * kInput,
+                                 c.n_chan, cudaMemcpyDeviceToDevice, p->stream));
+        }
+    }
+    cudaEvent_t ev;
+    if (!p->event_pool.empty()) {
+        ev = p->event_pool.back();
+        p->event_pool.pop_back();
+    } else {
+        CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    }
+    CK(cudaEventRecord(ev, p->stream));
+    InflightBatch ib{p->next_batch++, ev, {}, bytes};
+    for (auto& jb : jobs) {
+        ib.tickets.push_back(jb.ticket);
+        Ticket& t = p->tickets[jb.ticket];
+        t.state = T_INFLIGHT;
+        t.batch = ib.id;
+    }
+    for (auto& c : carries) {
+        if (c.drop) {
+            CK(cudaFreeAsync(c.st->carry, p->stream));
+            p->streams.erase(c.sid);
+        }
+    }
+    p->inflight.push_back(std::move(ib));
+    return BF_OK;
+}
+
+// Retire finished batches (caller holds the lock).  Returns true if any.
+bool retire(bf_plan_s* p) {
+    bool any = false;
+    while (!p->inflight.empty()) {
+        InflightBatch& ib = p->inflight.front();
+        cudaError_t e = cudaEventQuery(ib.ev);
+        if (e == cudaErrorNotReady) break;
+        for (uint64_t t : ib.tickets) {
+            auto it = p->tickets.find(t);
+            if (it == p->tickets.end()) continue;
+            if (e == cudaSuccess) {
+                it->second.state = T_DONE;
+            } else {
+                it->second.state = T_ERROR;
+                it->second.err = BF_ECUDA;
+                it->second.msg = std::string("batch failed: ") + cudaGetErrorString(e);
+            }
+        }
+        p->mem_in_use -= std::min(p->mem_in_use, ib.bytes);
+        p->event_pool.push_back(ib.ev);
+        p->inflight.pop_front();
+        any = true;
+    }
+    if (any) p->cv.notify_all();
+    return any;
+}
+
+void worker_main(bf_plan_s* p) {
+    cudaSetDevice(p->device);
+    std::unique_lock<std::mutex> lk(p->mu);
+    for (;;) {
+        retire(p);
+        // form the next batch: FIFO, one request per stream, within the budget
+        std::vector<Job> jobs;
+        size_t bytes = 0;
+        int segs = 0;
+        if ((int)p->inflight.size() < kMaxInflight) {
+            std::vector<uint64_t> taken_streams;
+            for (auto it = p->queue.begin(); it != p->queue.end();) {
+                const uint64_t sid = it->req.stream_id;
+                bool stream_seen = std::find(taken_streams.begin(), taken_streams.end(), sid) != taken_streams.end();
+                // keep per-stream order: a stream blocked here blocks its later requests
+                taken_streams.push_back(sid);
+                if (stream_seen) {
+                    ++it;
+                    continue;
+                }
+                Ticket& t = p->tickets[it->ticket];
+                const size_t budget = p->cfg.mem_budget;
+                if ((budget && p->mem_in_use + bytes + t.bytes > budget) || segs + it->req.n_chan > 8 * kMaxSegs) {
+                    ++it;
+                    continue;
+                }
+                bytes += t.bytes;
+                segs += it->req.n_chan;
+                jobs.push_back(std::move(*it));
+                it = p->queue.erase(it);
+            }
+        }
+        if (!jobs.empty()) {
+            p->mem_in_use += bytes;
+            int rc = launch_jobs(p, jobs, bytes);
+            if (rc) {
+                for (auto& jb : jobs) {
+                    Ticket& t = p->tickets[jb.ticket];
+                    t.state = T_ERROR;
+                    t.err = rc;
+                    t.msg = g_err;
+                }
+                p->mem_in_use -= std::min(p->mem_in_use, bytes);
+                p->cv.notify_all();
+            }
+            continue;
+        }
+        if (p->stop && p->queue.empty() && p->inflight.empty()) break;
+        if (p->inflight.empty())
+            p->cv.wait(lk);
+        else
+            p->cv.wait_for(lk, std::chrono::microseconds(20));
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* bf_last_error(void) { return g_err.c_str(); }
+
+int bf_config_default(bf_config* cfg) {
+    if (!cfg) return fail(BF_EINVAL, "null config");
+    std::memset(cfg, 0, sizeof *cfg);
+    cfg->n_cyl = kCyl;
+    cfg->n_feed = kFeed;
+    cfg->n_pol = kPol;
+    cfg->pad = kBins / kFeed;
+    cfg->n_ew = kEw;
+    cfg->upchan = kUp;
+    cfg->f_ds = kFds;
+    cfg->t_ds = kTds;
+    cfg->feed_spacing_m = 0.3048;
+    cfg->cyl_spacing_m = 20.0;
+    cfg->dt_s = 2.56e-6;
+    cfg->form = BF_FP32_FFT;
+    cfg->mode = BF_MODE_DIRECT;
+    cfg->device = -1;
+    return BF_OK;
+}
+
+int bf_plan(const bf_config* cfg, bf_plan_t* out) {
+    if (!cfg || !out) return fail(BF_EINVAL, "null argument");
+    *out = nullptr;
+    if (cfg->n_cyl != kCyl || cfg->n_feed != kFeed || cfg->n_pol != kPol || cfg->pad * kFeed != kBins ||
+        cfg->n_ew != kEw || cfg->upchan != kUp || cfg->f_ds != kFds || cfg->t_ds != kTds)
+        return fail(BF_EINVAL, "geometry differs from the one the kernels are built for (4x256x2, P=2, 4 E-W, 128/8/3)");
+    if (!(cfg->feed_spacing_m > 0) || !(cfg->cyl_spacing_m >= 0) || !std::isfinite(cfg->feed_spacing_m) ||
+        !std::isfinite(cfg->cyl_spacing_m))
+        return fail(BF_EINVAL, "bad spacings");
+    if (cfg->form != BF_FP32_FFT) return fail(BF_EINVAL, "form not available in this build");
+    if (cfg->mode != BF_MODE_DIRECT && cfg->mode != BF_MODE_SERVING) return fail(BF_EINVAL, "bad mode");
+    if (cfg->max_streams < 0) return fail(BF_EINVAL, "negative max_streams");
+
+    std::unique_ptr<bf_plan_s> p(new bf_plan_s);
+    p->cfg = *cfg;
+    p->ns_sin.resize(kNs);
+    p->ew_sin.resize(kEw);
+    int prc = fill_pointings(p.get(), cfg);
+    if (prc) return prc;
+    p->cfg.ns_sin = nullptr;
+    p->cfg.ew_sin = nullptr;
+
+    if (cfg->device >= 0) {
+        CK(cudaSetDevice(cfg->device));
+        p->device = cfg->device;
+    } else {
+        CK(cudaGetDevice(&p->device));
+    }
+    int major = 0, minor = 0;
+    CK(cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, p->device));
+    CK(cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, p->device));
+    if (major != 10 || minor != 3)
+        return fail(BF_EINVAL, "this library is built for sm_103a (GB300) only; device is sm_" +
+                                   std::to_string(major) + std::to_string(minor));
+    p->grid = fused_fp32_max_grid(p->device);
+    if (p->grid <= 0) return fail(BF_ECUDA, "cannot query SM count");
+
+    if (cfg->cuda_stream) {
+        p->stream = (cudaStream_t)cfg->cuda_stream;
+    } else {
+        CK(cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking));
+        p->own_stream = true;
+    }
+    CK(cudaMalloc(&p->d_lut, (size_t)kTableCap * kNs * sizeof(int16_t)));
+    CK(cudaMalloc(&p->d_ew, (size_t)kTableCap * kEw * kCyl * sizeof(float2)));
+    CK(cudaMalloc(&p->d_tw512, kBins * sizeof(float2)));
+    CK(cudaMalloc(&p->d_tw128, kUp * sizeof(float2)));
+    std::vector<float2> tw(kBins);
+    for (int e = 0; e < kBins; ++e)
+        tw[e] = make_float2((float)std::cos(-2.0 * kPi * e / kBins), (float)std::sin(-2.0 * kPi * e / kBins));
+    CK(cudaMemcpy(p->d_tw512, tw.data(), kBins * sizeof(float2), cudaMemcpyHostToDevice));
+    for (int e = 0; e < kUp; ++e)
+        tw[e] = make_float2((float)std::cos(-2.0 * kPi * e / kUp), (float)std::sin(-2.0 * kPi * e / kUp));
+    CK(cudaMemcpy(p->d_tw128, tw.data(), kUp * sizeof(float2), cudaMemcpyHostToDevice));
+
+    if (p->cfg.mode == BF_MODE_SERVING) {
+        bf_plan_s* raw = p.get();
+        raw->worker = std::thread(worker_main, raw);
+    }
+    *out = p.release();
+    return BF_OK;
+}
+
+int bf_frames_out(bf_plan_t p, uint64_t stream_id, int64_t n_samples, int64_t* n_frames_out) {
+    if (!p || !n_frames_out || n_samples < 0) return fail(BF_EINVAL, "bad argument");
+    std::lock_guard<std::mutex> lk(p->mu);
+    int carry = 0;
+    auto it = p->streams.find(stream_id);
+    if (it != p->streams.end()) carry = it->second.carry_rows;
+    // queued requests of this stream advance the carry too
+    for (auto& jb : p->queue)
+        if (jb.req.stream_id == stream_id) carry = (int)((carry + jb.req.n_samples) % kFrame);
+    *n_frames_out = (carry + n_samples) / kFrame;
+    return BF_OK;
+}
+
+int bf_submit(bf_plan_t p, const bf_request* r, uint64_t* ticket) {
+    if (!p || !ticket) return fail(BF_EINVAL, "null argument");
+    int rc = validate_request(r);
+    if (rc) return rc;
+    CK(cudaSetDevice(p->device));
+    std::unique_lock<std::mutex> lk(p->mu);
+    if (p->stop) return fail(BF_ESHUTDOWN, "plan is shutting down");
+    auto sit = p->streams.find(r->stream_id);
+    if (sit != p->streams.end() && sit->second.n_chan != r->n_chan)
+        return fail(BF_EINVAL, "stream changed its channel count");
+    if (r->n_samples > 0 && !r->out) {
+        int carry = sit != p->streams.end() ? sit->second.carry_rows : 0;
+        for (auto& jb : p->queue)
+            if (jb.req.stream_id == r->stream_id) carry = (int)((carry + jb.req.n_samples) % kFrame);
+        if ((carry + r->n_samples) / kFrame > 0) return fail(BF_EINVAL, "null out with frames to write");
+    }
+    Job jb;
+    jb.ticket = p->next_ticket++;
+    jb.req = *r;
+    jb.freqs.assign(r->chan_freq_hz, r->chan_freq_hz + r->n_chan);
+    jb.req.chan_freq_hz = jb.freqs.data();
+    Ticket t;
+    t.bytes = request_bytes(r, (int64_t)(r->n_samples / kFrame) + 1, sit == p->streams.end());
+    if (p->cfg.mem_budget && t.bytes > p->cfg.mem_budget)
+        return fail(BF_ENOMEM, "request larger than the plan's memory budget");
+    p->tickets[jb.ticket] = t;
+    *ticket = jb.ticket;
+
+    if (p->cfg.mode == BF_MODE_DIRECT) {
+        std::vector<Job> jobs;
+        jobs.push_back(std::move(jb));
+        rc = launch_jobs(p, jobs, 0);
+        if (rc) {
+            p->tickets.erase(*ticket);
+            return rc;
+        }
+        return BF_OK;
+    }
+    const bool fits = !p->cfg.mem_budget || p->mem_in_use + t.bytes <= p->cfg.mem_budget;
+    p->queue.push_back(std::move(jb));
+    p->cv.notify_all();
+    return fits ? BF_OK : BF_EQUEUED;
+}
+
+int bf_poll(bf_plan_t p, uint64_t ticket, int64_t timeout_us, int64_t* n_frames_out) {
+    if (!p) return fail(BF_EINVAL, "null plan");
+    const auto t0 = std::chrono::steady_clock::now();
+    std::unique_lock<std::mutex> lk(p->mu);
+    for (;;) {
+        auto it = p->tickets.find(ticket);
+        if (it == p->tickets.end()) return fail(BF_ENOTICKET, "unknown ticket");
+        if (it->second.state == T_INFLIGHT) retire(p);
+        it = p->tickets.find(ticket);
+        if (it->second.state == T_DONE) {
+            if (n_frames_out) *n_frames_out = it->second.n_frames;
+            p->tickets.erase(it);
+            return BF_OK;
+        }
+        if (it->second.state == T_ERROR) {
+            int err = it->second.err;
+            g_err = it->second.msg;
+            p->tickets.erase(it);
+            return err;
+        }
+        const auto el = std::chrono::duration_cast<std::chrono::microseconds>(std::chrono::steady_clock::now() - t0).count();
+        if (timeout_us >= 0 && el >= timeout_us) return BF_PENDING;
+        // inflight: poll the event; queued: wait for the worker
+        p->cv.wait_for(lk, std::chrono::microseconds(it->second.state == T_INFLIGHT ? 10 : 200));
+    }
+}
+
+int bf_destroy(bf_plan_t p) {
+    if (!p) return fail(BF_EINVAL, "null plan");
+    cudaSetDevice(p->device);
+    {
+        std::lock_guard<std::mutex> lk(p->mu);
+        p->stop = true;
+        p->cv.notify_all();
+    }
+    if (p->worker.joinable()) p->worker.join();
+    int rc = BF_OK;
+    cudaError_t e = cudaStreamSynchronize(p->stream);
+    if (e != cudaSuccess) rc = cuda_fail(e, "cudaStreamSynchronize");
+    {
+        std::lock_guard<std::mutex> lk(p->mu);
+        retire(p);
+        for (auto& kv : p->streams) cudaFree(kv.second.carry);
+        for (auto& ib : p->inflight) cudaEventDestroy(ib.ev);
+        for (auto ev : p->event_pool) cudaEventDestroy(ev);
+    }
+    cudaFree(p->d_lut);
+    cudaFree(p->d_ew);
+    cudaFree(p->d_tw512);
+    cudaFree(p->d_tw128);
+    if (p->own_stream) cudaStreamDestroy(p->stream);
+    delete p;
+    return rc;
+}
+
+// ---- inspection entry points ------------------------------------------------------------
+
+int bf_debug_tables(const bf_config* cfg, double freq_hz, int32_t* lut_out, float* ew_out) {
+    if (!cfg || !(freq_hz > 0) || !std::isfinite(freq_hz)) return fail(BF_EINVAL, "bad argument");
+    bf_plan_s tmp;
+    tmp.cfg = *cfg;
+    tmp.ns_sin.resize(kNs);
+    tmp.ew_sin.resize(kEw);
+    int rc = fill_pointings(&tmp, cfg);
+    if (rc) return rc;
+    if (lut_out) clamp_table(&tmp, freq_hz, lut_out);
+    if (ew_out) ew_table(&tmp, freq_hz, ew_out);
+    return BF_OK;
+}
+
+int bf_debug_unpack(bf_plan_t p, const uint8_t* d_in, float* d_out, int64_t n) {
+    if (!p || n < 0 || (n > 0 && (!d_in || !d_out))) return fail(BF_EINVAL, "bad argument");
+    CK(cudaSetDevice(p->device));
+    CK(debug_unpack_launch(d_in, d_out, n, p->stream));
+    CK(cudaStreamSynchronize(p->stream));
+    return BF_OK;
+}
+
+int bf_debug_beams(bf_plan_t p, double freq_hz, const uint8_t* d_vin, int64_t n_samples, float* d_out) {
+    if (!p || n_samples < 0 || !(freq_hz > 0) || (n_samples > 0 && (!d_vin || !d_out)))
+        return fail(BF_EINVAL, "bad argument");
+    if (((uintptr_t)d_vin & 15) != 0) return fail(BF_EINVAL, "vin must be 16-byte aligned");
+    CK(cudaSetDevice(p->device));
+    int tab;
+    {
+        std::lock_guard<std::mutex> lk(p->mu);
+        int rc = table_for(p, freq_hz, &tab);
+        if (rc) return rc;
+    }
+    CK(debug_beams_launch(d_vin, n_samples, p->d_lut + (size_t)tab * kNs, p->d_ew + (size_t)tab * kEw * kCyl,
+                          p->d_tw512, reinterpret_cast<float2*>(d_out), p->stream));
+    CK(cudaStreamSynchronize(p->stream));
+    return BF_OK;
+}
+
+int bf_debug_upchan(bf_plan_t p, double freq_hz, const uint8_t* d_vin, int64_t n_samples, float* d_out) {
+    if (!p || n_samples < 0 || n_samples % kFrame != 0 || !(freq_hz > 0) || (n_samples > 0 && (!d_vin || !d_out)))
+        return fail(BF_EINVAL, "bad argument (n_samples must be a multiple of 384)");
+    if (((uintptr_t)d_vin & 15) != 0) return fail(BF_EINVAL, "vin must be 16-byte aligned");
+    CK(cudaSetDevice(p->device));
+    Batch b = make_batch(p);
+    {
+        std::lock_guard<std::mutex> lk(p->mu);
+        int rc = table_for(p, freq_hz, &b.segs[0].table);
+        if (rc) return rc;
+    }
+    const int nf = (int)(n_samples / kFrame);
+    b.n_segs = 1;
+    b.n_items = nf * kEw;
+    b.segs[0].vin = d_vin;
+    b.segs[0].n_frames = nf;
+    b.dump = reinterpret_cast<float2*>(d_out);
+    CK(fused_fp32_dump_launch(b, std::min(p->grid, std::max(b.n_items, 1)), p->stream));
+    CK(cudaStreamSynchronize(p->stream));
+    return BF_OK;
+}
+
+}  // extern "C"
