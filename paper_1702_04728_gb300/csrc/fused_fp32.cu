@@ -1,28 +1,33 @@
 // Fused FP32 fan-beam kernel for sm_103a (arXiv 1702.04728, Sec. 3).
 //
-// One CTA (512 threads, one per SM) owns a work item = (channel segment,
+// One CTA (256 threads, one per SM) owns a work item = (channel segment,
 // output frame F, E-W beam j) and runs six passes over it, one per
-// (128-sample block, polarisation):
+// (128-sample block, polarisation).  Arithmetic is packed FP32x2
+// (FFMA2 / FADD2) in structure-of-arrays form: every value is a pair of two
+// time samples (or two fine channels) that go through identical operations.
 //
-//  phase A (per iteration of 16 time samples, one warp per sample)
-//    * 128-bit loads of the packed row, unpack of the 4+4-bit nibbles (Table 1);
-//    * E-W phasing of the 4 cylinders toward beam j (Sec. 3) -- applied before
-//      the N-S transform, which is legal because both are linear and the
-//      phases do not depend on the feed;
-//    * zero-padded 512-point N-S FFT of the 256 feeds (Sec. 3.1) as two
-//      256-point FFTs (even and odd bins), each 16 x 16 in registers with one
-//      shared-memory transpose; all 512 bins go to a shared-memory row;
-//  gather + first up-channel pass (one thread per (N-S beam, time residue))
-//    * the 256 bins of the clamp table (Eq. 1) are picked from the rows, an
-//      8-point DFT over the 8 samples of one residue class runs in registers,
-//      and the twiddled result is parked in tensor memory (TMEM, 256 KB);
+//  phase A (8 iterations per pass, 16 time samples each)
+//    * warp w loads the row pair tau = 16 w + 2 it + {0, 1} with 128-bit loads,
+//      unpacks the 4+4-bit nibbles (Table 1) exactly, and forms E-W beam j
+//      (Sec. 3) -- applied before the N-S transform, legal because both are
+//      linear and the phases do not depend on the feed;
+//    * the warp pair (2q, 2q+1) shares the phased feed lines of its 4 rows; the
+//      even warp computes the even bins (FFT256 of y), the odd warp the odd
+//      bins (FFT256 of y exp(-i pi n / 256)) of the zero-padded 512-point
+//      N-S FFT (Sec. 3.1), each as 16 x 16 with one shared-memory transpose;
+//      all 512 bins of every row land in a shared-memory row;
+//  gather + first up-channel pass (thread = N-S beam m)
+//    * bin L(m) of the clamp table (Eq. 1) is picked from the 8 rows of each
+//      time residue pair, an 8-point DFT runs in registers, and the twiddled
+//      result is parked in tensor memory (TMEM);
 //  second up-channel pass (after the 128 samples of the block)
 //    * 16-point DFTs from TMEM complete the 128-point FFT (Sec. 3.2), then
 //      |.|^2 is accumulated into the 16 fftshifted sub-channels (Sec. 3).
 //
 // The corner turn of the paper's second kernel (time-slowest to
-// time-fastest) is the gather into TMEM lanes; nothing but packed input and
-// float output touches global memory.
+// time-fastest) is the gather into TMEM lanes: one (beam j, pol, block) is
+// 256 beams x 128 samples x 8 B = 256 KB = all of TMEM.  Only packed input
+// and float output touch global memory.
 #include "bf_internal.h"
 
 #include <cstdint>
@@ -30,29 +35,49 @@
 namespace chimebf {
 namespace {
 
-constexpr int kThreads = 512;
-constexpr int kWarps = kThreads / 32;
-constexpr int kScrStride = 17;                        // padded row (float2) of the per-warp scratch
-constexpr int kScrWarp = 2 * 16 * kScrStride;         // float2 per warp: 32 rows of 17
-constexpr int kBinsBuf = kWarps * kBins;              // float2 per bins buffer (16 rows of 512)
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;       // 8: warp w loads row pair a = w
+constexpr int kPairs = kWarps / 2;
 
-constexpr size_t kSmemBins = 2ull * kBinsBuf * sizeof(float2);          // 131072
-constexpr size_t kSmemScr = (size_t)kWarps * kScrWarp * sizeof(float2); // 69632
-constexpr size_t kSmemLut = kNs * sizeof(int);                          // 1024
-constexpr size_t kSmemTw = kUp * sizeof(float2);                        // 1024
-constexpr size_t kSmemTotal = kSmemBins + kSmemScr + kSmemLut + kSmemTw;
+// shared memory (float4 = one SoA pair: re0, re1, im0, im1)
+constexpr int kBinsF4 = kWarps * kBins;             // 8 row pairs x 512 bins
+constexpr int kYscF4 = 2 * kFeed;                    // per warp pair: 2 row pairs x 256 feeds
+constexpr int kTbF4 = 2 * kFeed;                     // per warp: 2 row pairs x 16 x 16
+constexpr size_t kSmemBins = (size_t)kBinsF4 * 16;
+constexpr size_t kSmemYsc = (size_t)kPairs * kYscF4 * 16;
+constexpr size_t kSmemTb = (size_t)kWarps * kTbF4 * 16;
+constexpr size_t kSmemLut = kNs * sizeof(int);
+constexpr size_t kSmemTw = 8 * 8 * 16;               // pair twiddles of the first up-channel pass
+constexpr size_t kSmemTotal = kSmemBins + kSmemYsc + kSmemTb + kSmemLut + kSmemTw;
 
 // ---------------------------------------------------------------------------
-// complex helpers and small DFTs with compile-time twiddles
+// packed FP32x2 helpers (sm_100+: FADD2 / FMUL2 / FFMA2)
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float2 operator+(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 operator-(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
-__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
-    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+struct cp {            // two complex values in SoA form
+    float2 re, im;
+};
+
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(make_float2(-1.f, -1.f), b, a); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 bc(float v) { return make_float2(v, v); }
+
+__device__ __forceinline__ cp cadd(cp a, cp b) { return {add2(a.re, b.re), add2(a.im, b.im)}; }
+__device__ __forceinline__ cp csub(cp a, cp b) { return {sub2(a.re, b.re), sub2(a.im, b.im)}; }
+// a * (-i)
+__device__ __forceinline__ cp cmul_neg_i(cp a) { return {a.im, mul2(a.re, bc(-1.f))}; }
+// a * (C + i S), C and S pairs (per element of the pair)
+__device__ __forceinline__ cp cmulp(cp a, float2 C, float2 S) {
+    return {fma2(a.im, make_float2(-S.x, -S.y), mul2(a.re, C)), fma2(a.re, S, mul2(a.im, C))};
 }
-__device__ __forceinline__ float2 mul_neg_i(float2 a) { return make_float2(a.y, -a.x); }
+__device__ __forceinline__ cp ld_cp(const float4* p) {
+    const float4 v = *p;
+    return {make_float2(v.x, v.y), make_float2(v.z, v.w)};
+}
+__device__ __forceinline__ void st_cp(float4* p, cp a) { *p = make_float4(a.re.x, a.re.y, a.im.x, a.im.y); }
 
-// cos(2 pi e / 32) for e = 0..31, rounded from double precision.
+// cos(2 pi e / 32), e = 0..31, rounded from double precision.
 __device__ __forceinline__ constexpr float cos32(int e) {
     constexpr float t[32] = {
         1.000000000e+00f, 9.807852804e-01f, 9.238795325e-01f, 8.314696123e-01f,
@@ -65,65 +90,60 @@ __device__ __forceinline__ constexpr float cos32(int e) {
         7.071067812e-01f, 8.314696123e-01f, 9.238795325e-01f, 9.807852804e-01f};
     return t[e & 31];
 }
-// sin(2 pi e / 32) = cos(2 pi (e - 8) / 32)
 __device__ __forceinline__ constexpr float sin32(int e) { return cos32(e - 8); }
 
 // a * exp(-2 pi i e / N) for N | 32 and a compile-time e (after unrolling).
 template <int N>
-__device__ __forceinline__ float2 twiddle(float2 a, int e) {
-    constexpr float r = 7.071067812e-01f;
+__device__ __forceinline__ cp twiddle(cp a, int e) {
     const int k = (e * (32 / N)) & 31;               // angle in units of 2 pi / 32
     switch (k) {
         case 0: return a;
-        case 4: return make_float2(r * (a.x + a.y), r * (a.y - a.x));
-        case 8: return mul_neg_i(a);
-        case 12: return make_float2(r * (a.y - a.x), -r * (a.x + a.y));
-        case 16: return make_float2(-a.x, -a.y);
-        case 20: return make_float2(-r * (a.x + a.y), r * (a.x - a.y));
-        case 24: return make_float2(-a.y, a.x);
-        case 28: return make_float2(r * (a.x - a.y), r * (a.x + a.y));
-        default: return cmul(a, make_float2(cos32(k), -sin32(k)));
+        case 8: return cmul_neg_i(a);
+        case 16: return {mul2(a.re, bc(-1.f)), mul2(a.im, bc(-1.f))};
+        case 24: return {mul2(a.im, bc(-1.f)), a.re};
+        default: return cmulp(a, bc(cos32(k)), bc(-sin32(k)));
     }
 }
 
-// In-place forward DFT4 (exp(-i ...)), natural order.
-__device__ __forceinline__ void dft4(float2& a0, float2& a1, float2& a2, float2& a3) {
-    const float2 s02 = a0 + a2, d02 = a0 - a2, s13 = a1 + a3, d13 = mul_neg_i(a1 - a3);
-    a0 = s02 + s13;
-    a2 = s02 - s13;
-    a1 = d02 + d13;
-    a3 = d02 - d13;
+__device__ __forceinline__ void dft4(cp& a0, cp& a1, cp& a2, cp& a3) {
+    const cp s02 = cadd(a0, a2), d02 = csub(a0, a2), s13 = cadd(a1, a3);
+    // (a1 - a3) * (-i) = (a1.im - a3.im) + i (a3.re - a1.re)
+    const cp d13 = {sub2(a1.im, a3.im), sub2(a3.re, a1.re)};
+    a0 = cadd(s02, s13);
+    a2 = csub(s02, s13);
+    a1 = cadd(d02, d13);
+    a3 = csub(d02, d13);
 }
 
-// In-place forward DFT8 (2 x 4): n = 2 n1 + n2, k = k1 + 4 k2.
-__device__ __forceinline__ void dft8(float2 (&x)[8]) {
+// forward DFT8 (2 x 4), natural order in and out
+__device__ __forceinline__ void dft8(cp (&x)[8]) {
     dft4(x[0], x[2], x[4], x[6]);
     dft4(x[1], x[3], x[5], x[7]);
     x[3] = twiddle<8>(x[3], 1);
     x[5] = twiddle<8>(x[5], 2);
     x[7] = twiddle<8>(x[7], 3);
-    float2 y[8];
+    cp y[8];
 #pragma unroll
     for (int k1 = 0; k1 < 4; ++k1) {
-        y[k1] = x[2 * k1] + x[2 * k1 + 1];
-        y[k1 + 4] = x[2 * k1] - x[2 * k1 + 1];
+        y[k1] = cadd(x[2 * k1], x[2 * k1 + 1]);
+        y[k1 + 4] = csub(x[2 * k1], x[2 * k1 + 1]);
     }
 #pragma unroll
     for (int k = 0; k < 8; ++k) x[k] = y[k];
 }
 
-// In-place forward DFT16 (4 x 4): n = 4 n1 + n2, k = k1 + 4 k2.
-__device__ __forceinline__ void dft16(float2 (&x)[16]) {
+// forward DFT16 (4 x 4), natural order in and out
+__device__ __forceinline__ void dft16(cp (&x)[16]) {
 #pragma unroll
     for (int n2 = 0; n2 < 4; ++n2) dft4(x[n2], x[4 + n2], x[8 + n2], x[12 + n2]);
 #pragma unroll
     for (int n2 = 1; n2 < 4; ++n2)
 #pragma unroll
         for (int k1 = 1; k1 < 4; ++k1) x[4 * k1 + n2] = twiddle<16>(x[4 * k1 + n2], n2 * k1);
-    float2 y[16];
+    cp y[16];
 #pragma unroll
     for (int k1 = 0; k1 < 4; ++k1) {
-        float2 a0 = x[4 * k1], a1 = x[4 * k1 + 1], a2 = x[4 * k1 + 2], a3 = x[4 * k1 + 3];
+        cp a0 = x[4 * k1], a1 = x[4 * k1 + 1], a2 = x[4 * k1 + 2], a3 = x[4 * k1 + 3];
         dft4(a0, a1, a2, a3);
         y[k1] = a0;
         y[k1 + 4] = a1;
@@ -135,78 +155,57 @@ __device__ __forceinline__ void dft16(float2 (&x)[16]) {
 }
 
 // ---------------------------------------------------------------------------
-// 4+4-bit unpack (Table 1): byte at position `pos` of `word`, high nibble real.
-// The nibble is placed in the mantissa of 2^23 so the conversion is exact.
+// 4+4-bit unpack (Table 1) of the same byte position in two rows.  The nibble
+// (already shifted by 4 q bits) sits in the mantissa of 2^23; one FFMA2 scales
+// it back by 16^-q and removes 2^23 and the +8 offset -- exact throughout.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float2 unpack_byte(uint32_t word, int pos) {
-    const uint32_t b = (word >> (8 * pos)) & 0xFFu;
-    return make_float2(__uint_as_float(0x4B000000u | (b >> 4)) - 8388616.0f,
-                       __uint_as_float(0x4B000000u | (b & 15u)) - 8388616.0f);
+template <int Q>
+__device__ __forceinline__ float2 nib2(uint32_t g0, uint32_t g1) {
+    constexpr uint32_t mask = 0xFu << (4 * Q);
+    constexpr float s = 1.0f / float(1u << (4 * Q));
+    const float f0 = __uint_as_float((g0 & mask) | 0x4B000000u);
+    const float f1 = __uint_as_float((g1 & mask) | 0x4B000000u);
+    return fma2(make_float2(f0, f1), bc(s), bc(-(8388608.0f * s + 8.0f)));
 }
 
 __device__ __forceinline__ uint32_t word_of(const uint4& v, int k) {
     return k == 0 ? v.x : (k == 1 ? v.y : (k == 2 ? v.z : v.w));
 }
 
-// ---------------------------------------------------------------------------
-// N-S + E-W for one time sample and polarisation, one warp.
-//   in[c]  16 bytes of cylinder c: feeds 8*lane .. 8*lane+7, both pols
-//   w[c]   E-W weight of cylinder c for the beam being formed
-//   post   per-lane twiddles exp(-2 pi i n2 (2 k1 + h) / 512), k1 = 0..15
-//   scr    this warp's scratch (kScrWarp float2)
-//   row    512 float2 of shared memory: the zero-padded N-S bins, bin L at row[L]
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ void ns_ew_row(const uint4 (&in)[kCyl], int pol, const float2 (&w)[kCyl],
-                                          const float2 (&post)[16], float2* scr, float2* row, int lane) {
-    // E-W phasing on the unpacked voltages, written as y[n2][n1] with n = 16 n1 + n2.
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        const int pos = ((i & 1) << 1) | pol;
-        float2 y = make_float2(0.f, 0.f);
-#pragma unroll
-        for (int c = 0; c < kCyl; ++c) {
-            const float2 x = unpack_byte(word_of(in[c], i >> 1), pos);
-            y.x += w[c].x * x.x - w[c].y * x.y;
-            y.y += w[c].x * x.y + w[c].y * x.x;
-        }
-        scr[(((lane & 1) << 3) | i) * kScrStride + (lane >> 1)] = y;
-    }
-    __syncwarp();
+// swizzles that make the 128-bit shared accesses conflict-free
+__device__ __forceinline__ int ysw(int n2, int n1) { return n2 * 16 + (n1 ^ ((n2 & 7) ^ ((n2 >> 3) << 2))); }
+__device__ __forceinline__ int tsw(int r, int c) { return r * 16 + (c ^ (r & 7)); }
+__device__ __forceinline__ int bsw(int L) { return L ^ ((L >> 3) & 1); }
 
-    // Lanes 0-15 form the even bins (FFT256 of y), lanes 16-31 the odd bins
-    // (FFT256 of y[n] exp(-i pi n / 256)).  Lane handles n2 = lane & 15.
-    const int n2 = lane & 15, h = lane >> 4;
-    float2 v[16];
+__device__ __forceinline__ void pair_sync(int id) { asm volatile("bar.sync %0, 64;" :: "r"(id) : "memory"); }
+
+// Per-lane twiddles of the N-S FFT: exp(-2 pi i n2 (2 k1 + h) / 512), k1 = 0..15.
+struct PostTw {
+    float2 C[16], S[16];
+};
+
+__device__ __forceinline__ void load_post(const float2* __restrict__ tw512, int n2, int h, PostTw& pt) {
 #pragma unroll
-    for (int n1 = 0; n1 < 16; ++n1) v[n1] = scr[n2 * kScrStride + n1];
-    // exp(-i pi n / 256) = exp(-2 pi i n1 / 32) exp(-2 pi i n2 / 512); the first
-    // factor here, the second folded into post[].
-#pragma unroll
-    for (int n1 = 1; n1 < 16; ++n1) {
-        const float cr = h ? cos32(n1) : 1.f;
-        const float ci = h ? -sin32(n1) : 0.f;
-        v[n1] = cmul(v[n1], make_float2(cr, ci));
+    for (int k1 = 0; k1 < 16; ++k1) {
+        const float2 w = tw512[(n2 * (2 * k1 + h)) & (kBins - 1)];
+        pt.C[k1] = bc(w.x);
+        pt.S[k1] = bc(w.y);
     }
-    dft16(v);
-#pragma unroll
-    for (int k1 = 0; k1 < 16; ++k1) v[k1] = cmul(v[k1], post[k1]);
-    __syncwarp();
-#pragma unroll
-    for (int k1 = 0; k1 < 16; ++k1) scr[((h << 4) | n2) * kScrStride + k1] = v[k1];
-    __syncwarp();
-    const int k1 = lane & 15;
-#pragma unroll
-    for (int j = 0; j < 16; ++j) v[j] = scr[((h << 4) | j) * kScrStride + k1];
-    dft16(v);
-    // bin of the 512-point padded FFT: L = 2 (k1 + 16 k2) + h
-#pragma unroll
-    for (int k2 = 0; k2 < 16; ++k2) row[2 * (k1 + 16 * k2) + h] = v[k2];
 }
 
-__device__ __forceinline__ void load_post(const float2* __restrict__ tw512, int lane, float2 (&post)[16]) {
-    const int n2 = lane & 15, h = lane >> 4;
+// E-W weights of cylinders 1..3 for one beam (cylinder 0 is the phase origin, weight 1).
+struct EwW {
+    float2 R[3], I[3], NI[3];
+};
+
+__device__ __forceinline__ void load_ew(const float2* __restrict__ ew, int table, int j, EwW& w) {
 #pragma unroll
-    for (int k1 = 0; k1 < 16; ++k1) post[k1] = tw512[(n2 * (2 * k1 + h)) & (kBins - 1)];
+    for (int c = 1; c < kCyl; ++c) {
+        const float2 v = ew[(table * kEw + j) * kCyl + c];
+        w.R[c - 1] = bc(v.x);
+        w.I[c - 1] = bc(v.y);
+        w.NI[c - 1] = bc(-v.y);
+    }
 }
 
 __device__ __forceinline__ void load_row(const uint8_t* p, int lane, uint4 (&in)[kCyl]) {
@@ -216,28 +215,107 @@ __device__ __forceinline__ void load_row(const uint8_t* p, int lane, uint4 (&in)
 }
 
 // ---------------------------------------------------------------------------
-// tensor-memory access (tcgen05), one warp per 32-lane quarter
+// Phase A for one warp of a warp pair.
+//   in0/in1  the two rows of this warp's row pair (slot e of the pair)
+//   sel      byte permutation selecting polarisation pol of two feeds
+//   ysc      the pair's phased feed lines [2 slots][16 n2][16 n1] (swizzled)
+//   tb       this warp's transpose scratch [2 slots][16][16]
+//   bins2    bins of the pair's row pair slot 0 (slot 1 at + kBins)
+// e = warp & 1: the half of the padded FFT this warp computes, and the slot
+// of the row pair it loads.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void tmem_st2(uint32_t taddr, float2 v) {
-    asm volatile("tcgen05.st.sync.aligned.32x32b.x2.b32 [%0], {%1, %2};"
-                 :: "r"(taddr), "r"(__float_as_uint(v.x)), "r"(__float_as_uint(v.y)) : "memory");
+__device__ __forceinline__ void phase_a(const uint4 (&in0)[kCyl], const uint4 (&in1)[kCyl], uint32_t sel,
+                                        const EwW& w, const PostTw& pt, float4* ysc, float4* tb, float4* bins2,
+                                        int e, int lane, int bar_id) {
+    // unpack + E-W: lane holds feeds 8 lane .. 8 lane + 7 of both rows
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        cp yA, yB;
+#pragma unroll
+        for (int c = 0; c < kCyl; ++c) {
+            const uint32_t g0 = __byte_perm(word_of(in0[c], k), 0u, sel);
+            const uint32_t g1 = __byte_perm(word_of(in1[c], k), 0u, sel);
+            const float2 xiA = nib2<0>(g0, g1), xrA = nib2<1>(g0, g1);
+            const float2 xiB = nib2<2>(g0, g1), xrB = nib2<3>(g0, g1);
+            if (c == 0) {
+                yA = {xrA, xiA};
+                yB = {xrB, xiB};
+            } else {
+                yA.re = fma2(xiA, w.NI[c - 1], fma2(xrA, w.R[c - 1], yA.re));
+                yA.im = fma2(xrA, w.I[c - 1], fma2(xiA, w.R[c - 1], yA.im));
+                yB.re = fma2(xiB, w.NI[c - 1], fma2(xrB, w.R[c - 1], yB.re));
+                yB.im = fma2(xrB, w.I[c - 1], fma2(xiB, w.R[c - 1], yB.im));
+            }
+        }
+        // feed n = 8 lane + 2k (+1): n2 = n & 15, n1 = n >> 4
+        const int n2 = ((lane & 1) << 3) | (2 * k), n1 = lane >> 1;
+        st_cp(ysc + e * kFeed + ysw(n2, n1), yA);
+        st_cp(ysc + e * kFeed + ysw(n2 + 1, n1), yB);
+    }
+    pair_sync(bar_id);
+
+    // lanes 0-15: row pair slot 0, lanes 16-31: slot 1; lane handles n2
+    const int rp = lane >> 4, n2 = lane & 15;
+    cp v[16];
+#pragma unroll
+    for (int n1 = 0; n1 < 16; ++n1) v[n1] = ld_cp(ysc + rp * kFeed + ysw(n2, n1));
+    if (e) {
+        // odd bins: input times exp(-i pi n / 256) = exp(-2 pi i n1 / 32) * exp(-2 pi i n2 / 512);
+        // the second factor is folded into the per-lane twiddles
+#pragma unroll
+        for (int n1 = 1; n1 < 16; ++n1) v[n1] = cmulp(v[n1], bc(cos32(n1)), bc(-sin32(n1)));
+    }
+    dft16(v);
+#pragma unroll
+    for (int k1 = 0; k1 < 16; ++k1) v[k1] = cmulp(v[k1], pt.C[k1], pt.S[k1]);
+#pragma unroll
+    for (int k1 = 0; k1 < 16; ++k1) st_cp(tb + rp * kFeed + tsw(n2, k1), v[k1]);
+    __syncwarp();
+    const int k1 = n2;
+#pragma unroll
+    for (int r = 0; r < 16; ++r) v[r] = ld_cp(tb + rp * kFeed + tsw(r, k1));
+    dft16(v);
+    // bin of the 512-point padded FFT: L = 2 (k1 + 16 k2) + e
+    float4* row = bins2 + rp * kBins;
+#pragma unroll
+    for (int k2 = 0; k2 < 16; ++k2) st_cp(row + bsw(2 * (k1 + 16 * k2) + e), v[k2]);
 }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float2 (&v)[16]) {
-    uint32_t r[32];
+// ---------------------------------------------------------------------------
+// tensor-memory access (tcgen05), one warp per 32-lane quarter
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void tmem_st4(uint32_t taddr, float a, float b, float c, float d) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};"
+                 :: "r"(taddr), "r"(__float_as_uint(a)), "r"(__float_as_uint(b)), "r"(__float_as_uint(c)),
+                    "r"(__float_as_uint(d))
+                 : "memory");
+}
+
+// 64 consecutive columns: two fine channels c, c+1 x 16 residues b, as SoA pairs
+__device__ __forceinline__ void tmem_ld64(uint32_t taddr, cp (&y)[16]) {
+    uint32_t r[64];
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "tcgen05.ld.sync.aligned.32x32b.x64.b32 "
         "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n\t"
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, "
+        "%32, %33, %34, %35, %36, %37, %38, %39, %40, %41, %42, %43, %44, %45, %46, %47, "
+        "%48, %49, %50, %51, %52, %53, %54, %55, %56, %57, %58, %59, %60, %61, %62, %63}, [%64];\n\t"
         "tcgen05.wait::ld.sync.aligned;"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
           "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
           "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]),
+          "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]),
+          "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]),
+          "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]),
+          "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
         : "r"(taddr)
         : "memory");
 #pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = make_float2(__uint_as_float(r[2 * i]), __uint_as_float(r[2 * i + 1]));
+    for (int b = 0; b < 16; ++b) {
+        y[b].re = make_float2(__uint_as_float(r[2 * b]), __uint_as_float(r[32 + 2 * b]));
+        y[b].im = make_float2(__uint_as_float(r[2 * b + 1]), __uint_as_float(r[32 + 2 * b + 1]));
+    }
 }
 
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
@@ -259,21 +337,22 @@ __device__ __forceinline__ const uint8_t* frame_row(const Seg& sg, long long row
 template <bool kDump>
 __global__ void __launch_bounds__(kThreads, 1) fused_fp32_kernel(const __grid_constant__ Batch bt) {
     extern __shared__ __align__(16) unsigned char smem[];
-    float2* bins = reinterpret_cast<float2*>(smem);
-    float2* scr_all = reinterpret_cast<float2*>(smem + kSmemBins);
-    int* lut_s = reinterpret_cast<int*>(smem + kSmemBins + kSmemScr);
-    float2* tw128_s = reinterpret_cast<float2*>(smem + kSmemBins + kSmemScr + kSmemLut);
+    float4* bins = reinterpret_cast<float4*>(smem);
+    float4* ysc_all = reinterpret_cast<float4*>(smem + kSmemBins);
+    float4* tb_all = reinterpret_cast<float4*>(smem + kSmemBins + kSmemYsc);
+    int* lut_s = reinterpret_cast<int*>(smem + kSmemBins + kSmemYsc + kSmemTb);
+    float4* tw_s = reinterpret_cast<float4*>(smem + kSmemBins + kSmemYsc + kSmemTb + kSmemLut);
     __shared__ uint32_t tmem_base_s;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    float2* scr = scr_all + warp * kScrWarp;
+    const int e = warp & 1, q = warp >> 1;
+    float4* ysc = ysc_all + q * kYscF4;
+    float4* tb = tb_all + warp * kTbF4;
+    float4* bins2 = bins + (2 * q) * kBins;
 
-    // roles of the gather / second pass: TMEM lane quarter = warp & 3
-    const int ell = 32 * (warp & 3) + lane;     // TMEM lane
-    const int rsel = warp >> 2;                  // 0..3
-    const int hh = rsel & 1;                     // N-S beam half: m = ell + 128 hh
-    const int bsel = rsel >> 1;                  // gather: which of the two time residues
-    const int chalf = rsel >> 1;                 // second pass: fine-channel half
+    // gather / second pass role: TMEM lane quarter = warp & 3, bin half = warp >> 2
+    const int ell = 32 * (warp & 3) + lane;
+    const int hh = warp >> 2;
     const int m = ell + 128 * hh;
 
     if (warp == 0) {
@@ -281,16 +360,21 @@ __global__ void __launch_bounds__(kThreads, 1) fused_fp32_kernel(const __grid_co
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" :: "r"(dst) : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    for (int i = tid; i < kUp; i += kThreads) tw128_s[i] = bt.tw128[i];
+    // pair twiddles of the first up-channel pass: (b0, b1) = (2 it, 2 it + 1), c = 0..7
+    for (int i = tid; i < 64; i += kThreads) {
+        const int it = i >> 3, c = i & 7;
+        const float2 w0 = bt.tw128[(2 * it * c) & (kUp - 1)];
+        const float2 w1 = bt.tw128[((2 * it + 1) * c) & (kUp - 1)];
+        tw_s[i] = make_float4(w0.x, w1.x, w0.y, w1.y);
+    }
     cta_sync();
     const uint32_t tmem = tmem_base_s;
     const uint32_t tlane = tmem + (static_cast<uint32_t>(32 * (warp & 3)) << 16);
 
-    float2 post[16];
-    load_post(bt.tw512, lane, post);
+    PostTw pt;
+    load_post(bt.tw512, lane & 15, e, pt);
 
     for (int item = blockIdx.x; item < bt.n_items; item += gridDim.x) {
-        // locate the segment (descriptors are in kernel-parameter space)
         int sgi = 0;
         while (sgi + 1 < bt.n_segs && bt.segs[sgi + 1].item_begin <= item) ++sgi;
         const Seg& sg = bt.segs[sgi];
@@ -298,89 +382,91 @@ __global__ void __launch_bounds__(kThreads, 1) fused_fp32_kernel(const __grid_co
         const int F = local >> 2, j = local & 3;
 
         for (int i = tid; i < kNs; i += kThreads) lut_s[i] = bt.lut[sg.table * kNs + i];
-        float2 w[kCyl];
-#pragma unroll
-        for (int c = 0; c < kCyl; ++c) w[c] = bt.ew[(sg.table * kEw + j) * kCyl + c];
+        EwW w;
+        load_ew(bt.ew, sg.table, j, w);
         cta_sync();
-        const int L = lut_s[m];
+        const int Lsw = bsw(lut_s[m]);
 
-        float acc[kSub];
+        float2 acc[kSub];
 #pragma unroll
-        for (int s = 0; s < kSub; ++s) acc[s] = 0.f;
+        for (int s = 0; s < kSub; ++s) acc[s] = make_float2(0.f, 0.f);
 
         const long long row0 = (long long)F * kFrame;
-        uint4 cur[kCyl];
-        load_row(frame_row(sg, row0 + 16 * (warp & 7) + (warp >> 3)), lane, cur);
+        uint4 cur0[kCyl], cur1[kCyl];
+        load_row(frame_row(sg, row0 + 16 * warp), lane, cur0);
+        load_row(frame_row(sg, row0 + 16 * warp + 1), lane, cur1);
 
         for (int ps = 0; ps < kTds * kPol; ++ps) {
             const int blk = ps >> 1, pol = ps & 1;
+            const uint32_t sel = 0x4400u | ((2u + pol) << 4) | (uint32_t)pol;
             for (int it = 0; it < 8; ++it) {
-                // prefetch the row this warp needs next
-                uint4 nxt[kCyl];
-                const int nit = it < 7 ? it + 1 : 0;
-                const int nblk = it < 7 ? blk : ((ps + 1) >> 1);
+                uint4 nxt0[kCyl], nxt1[kCyl];
                 const bool more = it < 7 || ps + 1 < kTds * kPol;
                 if (more) {
-                    const long long r = row0 + nblk * kUp + 16 * (warp & 7) + 2 * nit + (warp >> 3);
-                    load_row(frame_row(sg, r), lane, nxt);
+                    const int nit = it < 7 ? it + 1 : 0;
+                    const int nblk = it < 7 ? blk : ((ps + 1) >> 1);
+                    const long long r = row0 + nblk * kUp + 16 * warp + 2 * nit;
+                    load_row(frame_row(sg, r), lane, nxt0);
+                    load_row(frame_row(sg, r + 1), lane, nxt1);
                 }
-                // phase A: this warp's time sample tau = 16 (warp & 7) + 2 it + (warp >> 3)
-                float2* rowbuf = bins + (it & 1) * kBinsBuf + warp * kBins;
-                ns_ew_row(cur, pol, w, post, scr, rowbuf, lane);
+                phase_a(cur0, cur1, sel, w, pt, ysc, tb, bins2, e, lane, 1 + q);
                 cta_sync();
-                // gather + 8-point DFT over a (tau = 16 a + b), twiddle exp(-2 pi i b c / 128)
+                // gather + 8-point DFT over a (tau = 16 a + b, b = 2 it, 2 it + 1)
                 {
-                    const float2* bb = bins + (it & 1) * kBinsBuf + (8 * bsel) * kBins + L;
-                    float2 z[8];
+                    cp z[8];
 #pragma unroll
-                    for (int a = 0; a < 8; ++a) z[a] = bb[a * kBins];
+                    for (int a = 0; a < 8; ++a) z[a] = ld_cp(bins + a * kBins + Lsw);
                     dft8(z);
-                    const int b = 2 * it + bsel;
+                    const int b0 = 2 * it;
 #pragma unroll
-                    for (int c = 1; c < 8; ++c) z[c] = cmul(z[c], tw128_s[(b * c) & (kUp - 1)]);
-#pragma unroll
-                    for (int c = 0; c < 8; ++c) tmem_st2(tlane + hh * 256 + 32 * c + 2 * b, z[c]);
+                    for (int c = 0; c < 8; ++c) {
+                        if (c) {
+                            const float4 t = tw_s[it * 8 + c];
+                            z[c] = cmulp(z[c], make_float2(t.x, t.y), make_float2(t.z, t.w));
+                        }
+                        tmem_st4(tlane + hh * 256 + 2 * (16 * c + b0), z[c].re.x, z[c].im.x, z[c].re.y, z[c].im.y);
+                    }
                 }
+                cta_sync();
                 if (more) {
 #pragma unroll
-                    for (int c = 0; c < kCyl; ++c) cur[c] = nxt[c];
+                    for (int c = 0; c < kCyl; ++c) {
+                        cur0[c] = nxt0[c];
+                        cur1[c] = nxt1[c];
+                    }
                 }
             }
             tmem_wait_st();
             cta_sync();
-            // second pass: 16-point DFT over b for fine channels q = c + 8 d
+            // second pass: 16-point DFT over b for fine channels q = c + 8 d, two c at a time
 #pragma unroll 1
-            for (int cc = 0; cc < 4; ++cc) {
-                const int c = 4 * chalf + cc;
-                float2 y[16];
-                tmem_ld32(tlane + hh * 256 + 32 * c, y);
+            for (int cpi = 0; cpi < 4; ++cpi) {
+                cp y[16];
+                tmem_ld64(tlane + hh * 256 + 64 * cpi, y);
                 dft16(y);
                 if constexpr (kDump) {
                     float2* d = bt.dump + ((((long long)(F * kTds + blk) * kPol + pol) * kEw + j) * kNs + m) * kUp;
 #pragma unroll
-                    for (int dd = 0; dd < 16; ++dd) d[(c + 8 * dd + kUp / 2) & (kUp - 1)] = y[dd];
+                    for (int dd = 0; dd < 16; ++dd) {
+                        const int c0 = 2 * cpi;
+                        d[(c0 + 8 * dd + kUp / 2) & (kUp - 1)] = make_float2(y[dd].re.x, y[dd].im.x);
+                        d[(c0 + 1 + 8 * dd + kUp / 2) & (kUp - 1)] = make_float2(y[dd].re.y, y[dd].im.y);
+                    }
                 } else {
 #pragma unroll
-                    for (int dd = 0; dd < 16; ++dd) acc[(dd + 8) & 15] += y[dd].x * y[dd].x + y[dd].y * y[dd].y;
+                    for (int dd = 0; dd < 16; ++dd) {
+                        const float2 p = fma2(y[dd].im, y[dd].im, mul2(y[dd].re, y[dd].re));
+                        acc[(dd + 8) & 15] = add2(acc[(dd + 8) & 15], p);
+                    }
                 }
             }
-            // the next pass's first gather overwrites TMEM: its barrier (after
-            // phase A) orders it after these loads.
+            // the next pass's first gather overwrites TMEM after two CTA barriers
         }
 
         if constexpr (!kDump) {
-            cta_sync();                                   // bins buffers free: reuse as combine area
-            float* comb = reinterpret_cast<float*>(bins);
-            if (chalf == 1) {
+            float* o = sg.out + (long long)(kNs * j + m) * sg.beam_stride + F;
 #pragma unroll
-                for (int s = 0; s < kSub; ++s) comb[m * 17 + s] = acc[s];
-            }
-            cta_sync();
-            if (chalf == 0) {
-                float* o = sg.out + (long long)(kNs * j + m) * sg.beam_stride + F;
-#pragma unroll
-                for (int s = 0; s < kSub; ++s) o[(long long)s * sg.sub_stride] = acc[s] + comb[m * 17 + s];
-            }
+            for (int s = 0; s < kSub; ++s) o[(long long)s * sg.sub_stride] = acc[s].x + acc[s].y;
         }
         cta_sync();
     }
@@ -394,39 +480,45 @@ __global__ void __launch_bounds__(kThreads, 1) fused_fp32_kernel(const __grid_co
 // ---------------------------------------------------------------------------
 // inspection kernels sharing the device code above
 // ---------------------------------------------------------------------------
-constexpr int kDbgWarps = 8;
 
-__global__ void __launch_bounds__(kDbgWarps * 32) debug_beams_kernel(const uint8_t* __restrict__ vin, long long T,
-                                                                     const int16_t* __restrict__ lut,
-                                                                     const float2* __restrict__ ew,
-                                                                     const float2* __restrict__ tw512,
-                                                                     float2* __restrict__ out) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float2* scr = reinterpret_cast<float2*>(smem) + warp * (kScrWarp + kBins);
-    float2* row = scr + kScrWarp;
-    const long long task = (long long)blockIdx.x * kDbgWarps + warp;   // (t, pol, j)
-    if (task >= T * kPol * kEw) return;
-    const int j = task % kEw, pol = (task / kEw) % kPol;
-    const long long t = task / (kEw * kPol);
-    float2 post[16];
-    load_post(tw512, lane, post);
-    float2 w[kCyl];
-#pragma unroll
-    for (int c = 0; c < kCyl; ++c) w[c] = ew[j * kCyl + c];
-    uint4 in[kCyl];
-    load_row(vin + t * kInput, lane, in);
-    ns_ew_row(in, pol, w, post, scr, row, lane);
-    __syncwarp();
-    float2* o = out + ((t * kPol + pol) * kEw + j) * kNs;
-    for (int mm = lane; mm < kNs; mm += 32) o[mm] = row[lut[mm]];
+// Stages 1+2 of 4 consecutive rows per CTA (one warp pair), then the clamp gather.
+__global__ void __launch_bounds__(64) debug_beams_kernel(const uint8_t* __restrict__ vin, long long T,
+                                                          const int16_t* __restrict__ lut,
+                                                          const float2* __restrict__ ew, const float2* __restrict__ tw512,
+                                                          float2* __restrict__ out) {
+    __shared__ float4 ysc[kYscF4];
+    __shared__ float4 tbs[2][kTbF4];
+    __shared__ float4 bins2[2 * kBins];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, e = warp;
+    const long long t0 = (long long)blockIdx.x * 4;
+    const int pol = blockIdx.y & 1, j = blockIdx.y >> 1;
+    PostTw pt;
+    load_post(tw512, lane & 15, e, pt);
+    EwW w;
+    load_ew(ew, 0, j, w);
+    uint4 in0[kCyl], in1[kCyl];
+    const long long ra = min(t0 + 2 * e, T - 1), rb = min(t0 + 2 * e + 1, T - 1);
+    load_row(vin + ra * kInput, lane, in0);
+    load_row(vin + rb * kInput, lane, in1);
+    const uint32_t sel = 0x4400u | ((2u + pol) << 4) | (uint32_t)pol;
+    phase_a(in0, in1, sel, w, pt, ysc, tbs[warp], bins2, e, lane, 1);
+    __syncthreads();
+    for (int i = threadIdx.x; i < 4 * kNs; i += 64) {
+        const int r = i >> 8, mm = i & 255;          // r: row 0..3 = slot (r >> 1), element (r & 1)
+        const long long t = t0 + r;
+        if (t >= T) continue;
+        const float4 v = bins2[(r >> 1) * kBins + bsw(lut[mm])];
+        out[((t * kPol + pol) * kEw + j) * kNs + mm] = (r & 1) ? make_float2(v.y, v.w) : make_float2(v.x, v.z);
+    }
 }
 
 __global__ void debug_unpack_kernel(const uint8_t* __restrict__ in, float2* __restrict__ out, long long n) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const uint32_t word = in[i];
-    out[i] = unpack_byte(word, 0);
+    // byte i goes through the same path as a polarisation-0 byte of a feed A
+    const uint32_t g = __byte_perm((uint32_t)in[i], 0u, 0x4420u);
+    const float2 re = nib2<1>(g, g), im = nib2<0>(g, g);
+    out[i] = make_float2(re.x, im.x);
 }
 
 }  // namespace
@@ -457,13 +549,9 @@ int fused_fp32_max_grid(int device) {
 
 cudaError_t debug_beams_launch(const uint8_t* vin, long long T, const int16_t* lut, const float2* ew,
                                const float2* tw512, float2* out, cudaStream_t s) {
-    const long long tasks = T * kPol * kEw;
-    if (tasks == 0) return cudaSuccess;
-    const size_t sm = (size_t)kDbgWarps * (kScrWarp + kBins) * sizeof(float2);
-    cudaError_t e = cudaFuncSetAttribute(debug_beams_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    debug_beams_kernel<<<(unsigned)((tasks + kDbgWarps - 1) / kDbgWarps), kDbgWarps * 32, sm, s>>>(vin, T, lut, ew,
-                                                                                                    tw512, out);
+    if (T == 0) return cudaSuccess;
+    dim3 grid((unsigned)((T + 3) / 4), kPol * kEw);
+    debug_beams_kernel<<<grid, 64, 0, s>>>(vin, T, lut, ew, tw512, out);
     return cudaGetLastError();
 }
 
