@@ -82,6 +82,7 @@ struct InflightBatch {
     cudaEvent_t ev;
     std::vector<uint64_t> tickets;
     size_t bytes;
+    std::vector<std::pair<size_t, uint8_t*>> release;   // carry buffers free once the batch is done
 };
 
 }  // namespace
@@ -109,7 +110,9 @@ struct bf_plan_s {
     std::deque<Job> queue;
     std::deque<InflightBatch> inflight;
     std::vector<cudaEvent_t> event_pool;
-    size_t mem_in_use = 0;
+    std::multimap<size_t, uint8_t*> carry_pool;   // free carry buffers by size (reused, freed at destroy)
+    size_t mem_in_use = 0;      // bytes of requests in launched, unretired batches
+    size_t queued_bytes = 0;    // bytes of requests waiting in the queue
     bool stop = false;
     std::thread worker;
 };
@@ -221,6 +224,19 @@ size_t request_bytes(const bf_request* r, int64_t nf, bool new_stream) {
     return b;
 }
 
+// Carry buffer of `bytes` from the plan's pool (or a new allocation).  Buffers
+// go back to the pool only after the batch that last used them has finished.
+int carry_alloc(bf_plan_s* p, size_t bytes, uint8_t** out) {
+    auto it = p->carry_pool.lower_bound(bytes);
+    if (it != p->carry_pool.end() && it->first == bytes) {
+        *out = it->second;
+        p->carry_pool.erase(it);
+        return BF_OK;
+    }
+    CK(cudaMalloc(out, bytes));
+    return BF_OK;
+}
+
 // Stream state for a request (created on first use).  Caller holds the lock.
 int stream_for(bf_plan_s* p, const bf_request* r, StreamState** out) {
     auto it = p->streams.find(r->stream_id);
@@ -238,8 +254,7 @@ int stream_for(bf_plan_s* p, const bf_request* r, StreamState** out) {
         int rc = table_for(p, r->chan_freq_hz[c], &s.tables[c]);
         if (rc) return rc;
     }
-    s.carry_bytes = (size_t)r->n_chan * (kFrame - 1) * kInput;
-    CK(cudaMalloc(&s.carry, s.carry_bytes));
+    s.carry_bytes = (size_t)r->n_chan * (kFrame - 1) * kInput;   // allocated when first needed
     auto res = p->streams.emplace(r->stream_id, std::move(s));
     *out = &res.first->second;
     return BF_OK;
@@ -277,7 +292,7 @@ int launch_jobs(bf_plan_s* p, std::vector<Job>& jobs, size_t bytes) {
             }
             Seg& s = b.segs[b.n_segs++];
             s.vin = jb.req.vin + (size_t)c * jb.req.n_samples * kInput;
-            s.carry = st->carry + (size_t)c * (kFrame - 1) * kInput;
+            s.carry = st->carry ? st->carry + (size_t)c * (kFrame - 1) * kInput : nullptr;
             s.out = jb.req.out + (size_t)kSub * c * nf;
             s.beam_stride = (long long)kSub * jb.req.n_chan * nf;
             s.sub_stride = (int)nf;
@@ -309,6 +324,10 @@ int launch_jobs(bf_plan_s* p, std::vector<Job>& jobs, size_t bytes) {
             rows = c.n;
         }
         if (rows > 0) {
+            if (!c.st->carry) {
+                int rc = carry_alloc(p, c.st->carry_bytes, &c.st->carry);
+                if (rc) return rc;
+            }
             CK(cudaMemcpy2DAsync(c.st->carry + dst_row * kInput, (size_t)(kFrame - 1) * kInput,
                                  c.vin + src_row * kInput, (size_t)c.n * kInput, (size_t)rows * kInput,
                                  c.n_chan, cudaMemcpyDeviceToDevice, p->stream));
@@ -322,7 +341,7 @@ int launch_jobs(bf_plan_s* p, std::vector<Job>& jobs, size_t bytes) {
         CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
     }
     CK(cudaEventRecord(ev, p->stream));
-    InflightBatch ib{p->next_batch++, ev, {}, bytes};
+    InflightBatch ib{p->next_batch++, ev, {}, bytes, {}};
     for (auto& jb : jobs) {
         ib.tickets.push_back(jb.ticket);
         Ticket& t = p->tickets[jb.ticket];
@@ -331,7 +350,7 @@ int launch_jobs(bf_plan_s* p, std::vector<Job>& jobs, size_t bytes) {
     }
     for (auto& c : carries) {
         if (c.drop) {
-            CK(cudaFreeAsync(c.st->carry, p->stream));
+            if (c.st->carry) ib.release.emplace_back(c.st->carry_bytes, c.st->carry);
             p->streams.erase(c.sid);
         }
     }
@@ -358,6 +377,7 @@ bool retire(bf_plan_s* p) {
             }
         }
         p->mem_in_use -= std::min(p->mem_in_use, ib.bytes);
+        for (auto& r : ib.release) p->carry_pool.emplace(r.first, r.second);
         p->event_pool.push_back(ib.ev);
         p->inflight.pop_front();
         any = true;
@@ -394,6 +414,7 @@ void worker_main(bf_plan_s* p) {
                 }
                 bytes += t.bytes;
                 segs += it->req.n_chan;
+                p->queued_bytes -= std::min(p->queued_bytes, t.bytes);
                 jobs.push_back(std::move(*it));
                 it = p->queue.erase(it);
             }
@@ -561,7 +582,9 @@ int bf_submit(bf_plan_t p, const bf_request* r, uint64_t* ticket) {
         }
         return BF_OK;
     }
-    const bool fits = !p->cfg.mem_budget || p->mem_in_use + t.bytes <= p->cfg.mem_budget;
+    // admitted at once only if it fits beside everything launched or queued before it
+    const bool fits = !p->cfg.mem_budget || p->mem_in_use + p->queued_bytes + t.bytes <= p->cfg.mem_budget;
+    p->queued_bytes += t.bytes;
     p->queue.push_back(std::move(jb));
     p->cv.notify_all();
     return fits ? BF_OK : BF_EQUEUED;
@@ -609,8 +632,13 @@ int bf_destroy(bf_plan_t p) {
     {
         std::lock_guard<std::mutex> lk(p->mu);
         retire(p);
-        for (auto& kv : p->streams) cudaFree(kv.second.carry);
-        for (auto& ib : p->inflight) cudaEventDestroy(ib.ev);
+        for (auto& kv : p->streams)
+            if (kv.second.carry) cudaFree(kv.second.carry);
+        for (auto& ib : p->inflight) {
+            cudaEventDestroy(ib.ev);
+            for (auto& r : ib.release) cudaFree(r.second);
+        }
+        for (auto& kv : p->carry_pool) cudaFree(kv.second);
         for (auto ev : p->event_pool) cudaEventDestroy(ev);
     }
     cudaFree(p->d_lut);

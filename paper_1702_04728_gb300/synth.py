@@ -158,16 +158,16 @@ def burst_amplitude(n_chan: int, sigma: float = 2.5, snr: float = 20.0) -> float
     return math.sqrt(snr * sigma * sigma / (1024.0 * math.sqrt(390.0 * 2.0 * n_chan)))
 
 
-def config_node_slice(seed: int = 0, n_samples: int = 49152):
-    """4 channels (410/520/650/790 MHz), 49152 samples, one DM-500 burst."""
-    freqs = [410e6, 520e6, 650e6, 790e6]
+def config_node_slice(seed: int = 0, n_samples: int = 49152, freqs=None):
+    """4 channels (410/520/650/790 MHz by default), 49152 samples, one DM-500 burst."""
+    freqs = list(freqs) if freqs is not None else [410e6, 520e6, 650e6, 790e6]
     rng = np.random.default_rng(seed + 1)
     m = int(rng.integers(0, 256))
     j = int(rng.integers(0, 4))
     s = (m - 127.5) / 128.0
     u = math.sin(math.radians([-0.6, -0.2, 0.2, 0.6][j]))
     b = Burst(burst_amplitude(len(freqs)), u=u, s=s, dm=500.0,
-              t0_s=0.5 * n_samples * DT_S, f_ref_hz=650e6)
+              t0_s=0.5 * n_samples * DT_S, f_ref_hz=freqs[2])
     raw = make_voltages(freqs, n_samples, seed, bursts=[b])
     return raw, np.array(freqs), {"burst_beam": 256 * j + m, "burst_chan": 2}
 
