@@ -116,7 +116,7 @@ def make_input(rank: int, world: int = 1):
     return raw, freqs
 
 
-def serving_run(B, torch, capacity_sps, load, seconds, n_streams=200, seed=0):
+def serving_run(B, torch, capacity_sps, load, seconds, n_streams=200, seed=0, form=0):
     """Poisson arrivals of frames (384..49152 samples, 1..16 channels per stream)
     from n_streams streams at `load` x capacity; returns latency percentiles."""
     import random
@@ -128,7 +128,7 @@ def serving_run(B, torch, capacity_sps, load, seconds, n_streams=200, seed=0):
     stream_chan = [rng.randint(1, max_chan) for _ in range(n_streams)]
     mean_samples = 8.5 * 384 * 64.5 * N_INPUT         # input-samples per request (mean)
     rate = load * capacity_sps / mean_samples          # requests per second
-    plan = B.Plan(mode=B.BF_MODE_SERVING, stream=None, mem_budget=40 << 30)
+    plan = B.Plan(mode=B.BF_MODE_SERVING, stream=None, mem_budget=40 << 30, form=form)
     freqs = {s: [400e6 + 390625.0 * (rng.randrange(1024) + 0.5) for _ in range(stream_chan[s])]
              for s in range(n_streams)}
     # warm the per-frequency tables
@@ -180,7 +180,7 @@ def serving_run(B, torch, capacity_sps, load, seconds, n_streams=200, seed=0):
             "sustained_samples_per_s": samples / elapsed, "streams": n_streams, "seconds": seconds}
 
 
-def cpu_baseline(raw, freqs, gpu_out=None, frames_per_chan: int = 16):
+def cpu_baseline(raw, freqs, gpu_out=None, form_outs=None, frames_per_chan: int = 16):
     """The FP64 oracle as it stands, on the first frames of every channel."""
     import oracle.chime_fftbf as O
     T = frames_per_chan * 384
@@ -194,6 +194,9 @@ def cpu_baseline(raw, freqs, gpu_out=None, frames_per_chan: int = 16):
     if gpu_out is not None:
         got = gpu_out[:, :, :frames_per_chan].astype(np.float64)
         res["max_rel_err_vs_gpu"] = float(np.max(np.abs(got - ref) / ref))
+    for name, o in (form_outs or {}).items():
+        got = o[:, :, :frames_per_chan].astype(np.float64)
+        res.setdefault("max_rel_err_by_form", {})[name] = float(np.max(np.abs(got - ref) / ref))
     return res
 
 
@@ -232,6 +235,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=30)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serving-seconds", type=float, default=2.0)
+    ap.add_argument("--form", default="BF_FP32_FFT",
+                    choices=["BF_FP32_FFT", "BF_TC_DFT256", "BF_TC_DFT256_X2", "BF_TC_DFT256_X1"])
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
@@ -271,6 +276,15 @@ def main():
         torch.cuda.synchronize()
 
     peaks, peak_kind = load_peaks()
+    form_names = {B.BF_FP32_FFT: "fp32_fft", B.BF_TC_DFT256: "tc_dft256_3term",
+                  B.BF_TC_DFT256_X2: "tc_dft256_2term", B.BF_TC_DFT256_X1: "tc_dft256_1term"}
+    headline_form = getattr(B, args.form)
+    if headline_form != B.BF_FP32_FFT:
+        plan.close()
+        plan = B.Plan(stream=stream, form=headline_form)
+        tickets = [step(1) for _ in range(args.warmup)]
+        for t in tickets:
+            plan.poll(t)
     with ClockSampler(local) as clk:
         barrier()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -282,6 +296,37 @@ def main():
             plan.poll(t)
         ms = ev0.elapsed_time(ev1) / args.steps
     clocks = clk.summary()
+
+    # every form on the same resident input (device-timed, same stream)
+    form_runs = []
+    form_outs = {}
+    for fid, fname in form_names.items():
+        fp = B.Plan(stream=stream, form=fid)
+        fo = torch.empty_like(out)
+        for _ in range(3):
+            _, t = fp.submit(vin, freqs, fo, stream_id=7, flags=B.BF_END_OF_STREAM)
+            fp.poll(t)
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        nrep = max(10, args.steps // 5)
+        e0.record(stream)
+        tk = [fp.submit(vin, freqs, fo, stream_id=7, flags=B.BF_END_OF_STREAM)[1] for _ in range(nrep)]
+        e1.record(stream)
+        barrier()
+        for t in tk:
+            fp.poll(t)
+        fms = e0.elapsed_time(e1) / nrep
+        fp.close()
+        terms = {B.BF_TC_DFT256: 3, B.BF_TC_DFT256_X2: 2, B.BF_TC_DFT256_X1: 1}.get(fid, 0)
+        samples_ = N_CHAN * N_SAMP * N_INPUT
+        run = {"form": fname, "ms_per_step": fms, "input_samples_per_s": samples_ / (fms * 1e-3)}
+        if terms:
+            tflops = 2048.0 * terms * samples_ / (fms * 1e-3) / 1e12
+            run["tensor_tflops"] = tflops
+            run["tensor_frac_of_measured_bf16_dense"] = tflops / peaks.get("bf16_tflops", 1927.5)
+            run["tensor_flop_per_sample"] = 2048 * terms
+        form_runs.append(run)
+        form_outs[fname] = fo[:, :, :16].cpu().numpy()
 
     # end to end through the public API: pinned host in -> device -> beamform -> host out.
     # One request per channel; the copy of channel c+1 overlaps the beamforming of c.
@@ -327,36 +372,48 @@ def main():
     value = samples * ws / (ms * 1e-3)
 
     if rank == 0:
-        sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
         n_sm = torch.cuda.get_device_properties(local).multi_processor_count
-        alu_peak = n_sm * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12   # FP32 TFLOP/s at max clock
-        achieved = FLOP_PER_SAMPLE * samples / (ms * 1e-3) / 1e12
         hbm_gbs = BYTES_PER_SAMPLE * samples / (ms * 1e-3) / 1e9
+        fname = form_names[headline_form]
+        terms = {B.BF_TC_DFT256: 3, B.BF_TC_DFT256_X2: 2, B.BF_TC_DFT256_X1: 1}.get(headline_form, 0)
+        if terms:
+            achieved = 2048.0 * terms * samples / (ms * 1e-3) / 1e12
+            roof = {"bound": "tensor", "achieved": achieved, "peak": peaks.get("bf16_tflops", 1927.5),
+                    "unit": "TFLOP/s", "frac": achieved / peaks.get("bf16_tflops", 1927.5), "traffic": None,
+                    "peak_note": f"dense FP16 tensor peak = measured bf16 burst ({peak_kind}; FP16 and BF16 "
+                                 f"share the rate); achieved = 2048 x {terms} GEMM flop per input-sample"}
+        else:
+            alu_peak = n_sm * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+            achieved = FLOP_PER_SAMPLE * samples / (ms * 1e-3) / 1e12
+            roof = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                    "frac": achieved / alu_peak, "traffic": None,
+                    "peak_note": f"FP32 FMA pipe: {n_sm} SMs x 128 lanes x 2 flop x "
+                                 f"{peaks.get('sm_max_mhz', 2070.0):.0f} MHz ({peak_kind} max clock); "
+                                 f"achieved = {FLOP_PER_SAMPLE:.0f} algorithmic flop per input-sample"}
         line = {
             "metric": METRIC, "value": value, "unit": "input-samples/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f16-tc/f32" if terms else "f32",
+            "data": "synthetic",
             "config": {"workload": WORKLOAD, "n_chan": N_CHAN, "n_samples": N_SAMP, "n_inputs": N_INPUT,
-                       "form": "fp32_fft", "output": "float32 [1024][64][128]",
+                       "form": fname, "output": "float32 [1024][64][128]",
                        "l2": "inputs (402.7 MB) larger than L2; no flush",
                        "hbm_gbs": hbm_gbs, "hbm_frac_of_measured": hbm_gbs / peaks["hbm_gbs"]},
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
-                         "frac": achieved / alu_peak, "traffic": None,
-                         "peak_note": f"FP32 FMA pipe: {n_sm} SMs x 128 lanes x 2 flop x "
-                                      f"{peaks.get('sm_max_mhz', 2070.0):.0f} MHz ({peak_kind} max clock); "
-                                      f"achieved = {FLOP_PER_SAMPLE:.0f} algorithmic flop per input-sample"},
+            "roofline": roof,
             "e2e": {"value": samples * ws / (e2e_ms * 1e-3), "unit": "input-samples/s",
                     "h2d_bytes_per_step": samples, "d2h_bytes_per_step": out.numel() * 4,
                     "ms_per_step": e2e_ms, "how": "wall clock; per-channel requests, H2D of channel c+1 "
                                                   "overlapping beamforming of channel c, D2H of each output"},
             "gpu_launches": args.steps,
+            "forms": form_runs,
             "clocks": clocks,
         }
         if args.serving_seconds > 0:
             cap = samples / (ms * 1e-3)
-            line["serving"] = [serving_run(B, torch, cap, ld, args.serving_seconds) for ld in (0.5, 0.9)]
+            line["serving"] = [serving_run(B, torch, cap, ld, args.serving_seconds, form=headline_form)
+                               for ld in (0.5, 0.9)]
         if not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline(raw, freqs, host_out.numpy())
+            line["cpu_baseline"] = cpu_baseline(raw, freqs, host_out.numpy(), form_outs)
         print(json.dumps(line), flush=True)
     plan.close()
     if ws > 1:

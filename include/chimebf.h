@@ -44,10 +44,15 @@ extern "C" {
 #define BF_ENOTICKET  -5   /* unknown, already collected or cancelled ticket        */
 #define BF_ESHUTDOWN  -6   /* plan is being destroyed                               */
 
-/* N-S transform forms (bf_config.form) */
-#define BF_FP32_FFT    0   /* FP32 zero-padded FFT on the CUDA cores                */
-#define BF_TC_DFT256   1   /* tensor-core DFT GEMM over the 256 clamped rows        */
-#define BF_TC_DFT512   2   /* tensor-core DFT GEMM over all 512 padded rows         */
+/* N-S transform forms (bf_config.form).  The tensor-core forms evaluate the
+ * clamped zero-padded FFT as the equivalent DFT over the 256 kept rows on
+ * tcgen05 (FP16 operands, FP32 accumulation); the E-W phased feed line is split
+ * into FP16 hi + lo, the twiddles are FP16 hi (+ lo). */
+#define BF_FP32_FFT      0 /* FP32 zero-padded FFT on the CUDA cores                */
+#define BF_TC_DFT256     1 /* 3 GEMM terms: twiddles hi+lo x data hi+lo             */
+#define BF_TC_DFT512     2 /* all 512 padded rows (same result as 256; not built)   */
+#define BF_TC_DFT256_X2  3 /* 2 GEMM terms: twiddles hi x data hi+lo                */
+#define BF_TC_DFT256_X1  4 /* 1 GEMM term: twiddles hi x data hi                    */
 
 /* execution modes (bf_config.mode) */
 #define BF_MODE_DIRECT   0 /* bf_submit launches at once on cuda_stream             */
@@ -82,7 +87,7 @@ typedef struct {
                                NULL for (m - 127.5)/128; copied by bf_plan        */
     const double* ew_sin;   /* host [n_ew] sin of the E-W beam angles, or NULL for
                                sin({-0.6, -0.2, 0.2, 0.6} deg); copied            */
-    int form;               /* BF_FP32_FFT | BF_TC_DFT256 | BF_TC_DFT512          */
+    int form;               /* BF_FP32_FFT or a BF_TC_DFT256* form                */
     int mode;               /* BF_MODE_DIRECT | BF_MODE_SERVING                   */
     size_t mem_budget;      /* serving admission budget in bytes (0 = unlimited)  */
     int max_streams;        /* distinct stream_ids held at once (0 = 1024)        */
@@ -155,6 +160,10 @@ const char* bf_last_error(void);
  * configuration cfg uses for one frequency.  Needs no GPU; either output may
  * be NULL. */
 int bf_debug_tables(const bf_config* cfg, double freq_hz, int32_t* lut_out, float* ew_out);
+
+/* Tensor-core forms only: the GEMM output (N-S beams after E-W phasing) as
+ * float2 [block][pol][ew][ns][t], t = 0..127, for n_samples a multiple of 384. */
+int bf_debug_gemm(bf_plan_t p, double freq_hz, const uint8_t* d_vin, int64_t n_samples, float* d_out);
 
 /* Device unpack of n bytes into 2n floats (re, im), with the same device
  * code the fused kernel uses.  d_in, d_out device pointers. */

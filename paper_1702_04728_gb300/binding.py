@@ -16,14 +16,15 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libchimebf.so")
 
 BF_OK, BF_PENDING, BF_EQUEUED = 0, 1, 2
 BF_EINVAL, BF_ENOMEM, BF_ECUDA, BF_ETIMEDOUT, BF_ENOTICKET, BF_ESHUTDOWN = -1, -2, -3, -4, -5, -6
-BF_FP32_FFT, BF_TC_DFT256, BF_TC_DFT512 = 0, 1, 2
+BF_FP32_FFT, BF_TC_DFT256, BF_TC_DFT512, BF_TC_DFT256_X2, BF_TC_DFT256_X1 = 0, 1, 2, 3, 4
 BF_MODE_DIRECT, BF_MODE_SERVING = 0, 1
 BF_END_OF_STREAM = 1
 
 N_BEAMS, N_SUB, FRAME, N_INPUT = 1024, 16, 384, 2048
 
 SYMBOLS = ["bf_config_default", "bf_plan", "bf_frames_out", "bf_submit", "bf_poll", "bf_destroy",
-           "bf_last_error", "bf_debug_tables", "bf_debug_unpack", "bf_debug_beams", "bf_debug_upchan"]
+           "bf_last_error", "bf_debug_tables", "bf_debug_gemm", "bf_debug_unpack", "bf_debug_beams",
+           "bf_debug_upchan"]
 
 
 class BfError(RuntimeError):
@@ -74,6 +75,7 @@ def lib() -> ctypes.CDLL:
         L.bf_debug_unpack.argtypes = [P, P, P, I64]
         L.bf_debug_beams.argtypes = [P, D, P, I64, P]
         L.bf_debug_upchan.argtypes = [P, D, P, I64, P]
+        L.bf_debug_gemm.argtypes = [P, D, P, I64, P]
         for name in SYMBOLS:
             getattr(L, name).restype = ctypes.c_char_p if name == "bf_last_error" else I
         _lib = L
@@ -189,6 +191,10 @@ def bf_debug_beams(plan: int, freq_hz: float, d_vin, n_samples: int, d_out) -> N
 
 def bf_debug_upchan(plan: int, freq_hz: float, d_vin, n_samples: int, d_out) -> None:
     _check(lib().bf_debug_upchan(plan, float(freq_hz), _ptr(d_vin), n_samples, _ptr(d_out)))
+
+
+def bf_debug_gemm(plan: int, freq_hz: float, d_vin, n_samples: int, d_out) -> None:
+    _check(lib().bf_debug_gemm(plan, float(freq_hz), _ptr(d_vin), n_samples, _ptr(d_out)))
 
 
 # ---- convenience over torch device memory (allocation and marshalling only) ----

@@ -48,6 +48,9 @@ struct Batch {
     const float2* tw512;     // [512] exp(-2 pi i e / 512)
     const float2* tw128;     // [128] exp(-2 pi i e / 128)
     float2* dump;            // debug: up-channelised voltages instead of detection
+    const unsigned char* a_tc;   // tensor-core form: FP16 twiddle images per table
+    size_t a_tc_stride;          // bytes per table in a_tc
+    int* status;                 // set non-zero by a kernel whose bounded wait expired
     Seg segs[kMaxSegs];
 };
 
@@ -58,5 +61,11 @@ cudaError_t debug_beams_launch(const uint8_t* vin, long long n_samples, const in
                                const float2* ew, const float2* tw512, float2* out, cudaStream_t s);
 cudaError_t debug_unpack_launch(const uint8_t* in, float* out, long long n, cudaStream_t s);
 int fused_fp32_max_grid(int device);   // CTAs that fit at once (1 per SM)
+
+// Tensor-core form: `terms` = 1, 2 or 3 GEMM terms; mode 0 = detect,
+// 1 = dump up-channelised voltages, 2 = dump the N-S/E-W beams of the GEMM.
+cudaError_t fused_tc_launch(const Batch& b, int terms, int mode, int grid, cudaStream_t s);
+size_t tc_a_bytes(int terms);    // bytes of one table's twiddle image(s)
+int tc_chunk_k(int terms);       // K elements per shared-memory chunk
 
 }  // namespace chimebf

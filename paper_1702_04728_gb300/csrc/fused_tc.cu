@@ -1,0 +1,406 @@
+// Tensor-core form of the fan-beam path for sm_103a (arXiv 1702.04728, Sec. 3).
+//
+// Same work decomposition as the FP32 kernel -- one CTA per SM owns
+// (channel segment, frame F, E-W beam j) and makes six passes (3 blocks x 2
+// pols) -- but the N-S stage (Sec. 3.1: zero-padded FFT kept at the 256 bins
+// of Eq. 1) is evaluated as the equivalent dense DFT over the clamped rows on
+// the tcgen05 tensor cores:
+//
+//   X[m][t] = sum_n exp(-2 pi i n L(m) / 512) y_j[n][t],   m < 256, n < 256,
+//
+// with y_j the E-W phased feed line (Sec. 3) of block time t.  As a real GEMM:
+// rows = bins m (two M = 128 tiles), columns = (t, re/im) (N = 256), K = (n,
+// re/im) = 512.  With A[m][2n] = cos, A[m][2n+1] = sin (of 2 pi n L / 512) the
+// column (t, 0) of B holds (yr, yi) and (t, 1) holds (yi, -yr), so the two
+// columns give Re and Im of X with one A.  The accumulator lands in tensor
+// memory exactly where the up-channel passes want it: lane = bin (m, m+128),
+// column 2t / 2t+1 = Re / Im of time t.
+//
+// Precision: FP16 operands, FP32 accumulation.  y is split y = y_hi + y_lo in
+// FP16 (22 bits together); the twiddles are FP16 (hi) and, for three terms,
+// also lo.  Terms: 1 = A_hi y_hi, 2 = + A_hi y_lo, 3 = + A_lo y_hi.
+//
+// Pipeline per pass: K is streamed in chunks through two shared-memory stages;
+// all warps build the B chunk (unpack, E-W, FP16 split) and copy the A chunk,
+// one thread issues the MMAs and commits them to the stage's mbarrier, which
+// the producers wait on before reusing the stage.  Every wait is bounded by
+// %globaltimer; on expiry the kernel records an error and leaves cleanly.
+#include "device_common.cuh"
+
+#include <cuda_fp16.h>
+
+#include <cstdint>
+
+namespace chimebf {
+namespace {
+
+constexpr int kTcThreads = 256;
+constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s bound on every mbarrier wait
+
+template <int TERMS>
+struct TcCfg {
+    static constexpr int KC = TERMS == 3 ? 32 : 64;              // K elements (FP16) per chunk
+    static constexpr int NCH = 2 * kFeed / KC;                    // chunks per pass
+    static constexpr int NQUAD = KC / 8;                          // 4-feed quads per chunk
+    static constexpr int SBO = KC / 8 * 128;                      // bytes between 8-row groups
+    static constexpr int OPER = 256 * KC * 2;                     // bytes of one 256-row operand chunk
+    static constexpr bool A_LO = TERMS == 3;
+    static constexpr bool B_LO = TERMS >= 2;
+    static constexpr int STAGE = OPER * (1 + (A_LO ? 1 : 0) + 1 + (B_LO ? 1 : 0));
+    static constexpr size_t SMEM = 2ull * STAGE + 8 * 8 * 16 + 64;   // + up-channel twiddles + barriers
+};
+
+// Byte offset of element (row r, k) in a K-major operand chunk without
+// swizzle: 8 x 16-byte core matrices, k-groups 128 B apart, row groups SBO apart.
+template <int SBO>
+__device__ __forceinline__ int core_off(int r, int kgroup) {
+    return (r >> 3) * SBO + kgroup * 128 + (r & 7) * 16;
+}
+
+// shared-memory matrix descriptor (no swizzle, version 1)
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46);
+}
+
+// instruction descriptor: kind::f16, A = B = F16, D = F32, both K-major, M = 128, N = 256
+constexpr uint32_t kIdesc = (1u << 4) | ((256u >> 3) << 17) | ((128u >> 4) << 24);
+
+__device__ __forceinline__ void mma_f16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t accum) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+        :: "r"(dtmem), "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accum)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t mbar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" :: "r"(mbar)
+                 : "memory");
+}
+
+__device__ __forceinline__ unsigned long long globaltimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait for the completion of phase `parity` of an mbarrier.
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+    const unsigned long long t0 = globaltimer();
+    for (;;) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok) : "r"(mbar), "r"(parity) : "memory");
+        if (ok) return true;
+        if (globaltimer() - t0 > kWaitNs) return false;
+    }
+}
+
+// Eight 4-column TMEM loads (columns base + 32 a .. + 3, a = 0..7) -> SoA pairs.
+__device__ __forceinline__ void tmem_ld8x4(uint32_t taddr, cp (&z)[8]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%32];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%4, %5, %6, %7}, [%33];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%8, %9, %10, %11}, [%34];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%12, %13, %14, %15}, [%35];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%16, %17, %18, %19}, [%36];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%20, %21, %22, %23}, [%37];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%24, %25, %26, %27}, [%38];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%28, %29, %30, %31}, [%39];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr), "r"(taddr + 32), "r"(taddr + 64), "r"(taddr + 96), "r"(taddr + 128), "r"(taddr + 160),
+          "r"(taddr + 192), "r"(taddr + 224)
+        : "memory");
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+        z[a].re = make_float2(__uint_as_float(r[4 * a]), __uint_as_float(r[4 * a + 2]));
+        z[a].im = make_float2(__uint_as_float(r[4 * a + 1]), __uint_as_float(r[4 * a + 3]));
+    }
+}
+
+__device__ __forceinline__ uint32_t h2u(__half2 h) { return *reinterpret_cast<uint32_t*>(&h); }
+
+// Build the B chunk `kc` of pass (blk, pol) for tasks (t, quad) of this thread:
+// unpack 4 feeds x 4 cylinders, E-W toward beam j, split into FP16 hi (+ lo),
+// and store rows (t, re-col) = (yr, yi) and (t, im-col) = (yi, -yr).
+template <int TERMS>
+__device__ __forceinline__ void produce_b(const Seg& sg, long long row0, int kc, uint32_t sel, const EwW& w,
+                                          unsigned char* bhi, unsigned char* blo, int tid) {
+    using C = TcCfg<TERMS>;
+    constexpr int TASKS = kUp * C::NQUAD / kTcThreads;       // 4 (KC 64) or 2 (KC 32)
+    const int quad = (tid >> 5) % C::NQUAD;
+    const int tbase = (tid & 31) + 32 * ((tid >> 5) / C::NQUAD);
+    const int n0 = (C::KC / 2) * kc + 4 * quad;             // first feed of the quad
+#pragma unroll
+    for (int i = 0; i < TASKS; ++i) {
+        const int t = tbase + i * (kTcThreads / C::NQUAD);
+        const uint8_t* rp = frame_row(sg, row0 + t) + 2 * n0;
+        uint2 in[kCyl];
+#pragma unroll
+        for (int c = 0; c < kCyl; ++c) in[c] = __ldg(reinterpret_cast<const uint2*>(rp + c * (kFeed * kPol)));
+        // SoA pairs: P0 = feeds (n0, n0 + 2), P1 = feeds (n0 + 1, n0 + 3)
+        cp y0, y1;
+#pragma unroll
+        for (int c = 0; c < kCyl; ++c) {
+            const uint32_t g0 = __byte_perm(in[c].x, 0u, sel), g1 = __byte_perm(in[c].y, 0u, sel);
+            const float2 xi0 = nib2<0>(g0, g1), xr0 = nib2<1>(g0, g1);
+            const float2 xi1 = nib2<2>(g0, g1), xr1 = nib2<3>(g0, g1);
+            if (c == 0) {
+                y0 = {xr0, xi0};
+                y1 = {xr1, xi1};
+            } else {
+                y0.re = fma2(xi0, w.NI[c - 1], fma2(xr0, w.R[c - 1], y0.re));
+                y0.im = fma2(xr0, w.I[c - 1], fma2(xi0, w.R[c - 1], y0.im));
+                y1.re = fma2(xi1, w.NI[c - 1], fma2(xr1, w.R[c - 1], y1.re));
+                y1.im = fma2(xr1, w.I[c - 1], fma2(xi1, w.R[c - 1], y1.im));
+            }
+        }
+        // feeds in k order: n0 (y0.x), n0+1 (y1.x), n0+2 (y0.y), n0+3 (y1.y)
+        const float yr[4] = {y0.re.x, y1.re.x, y0.re.y, y1.re.y};
+        const float yi[4] = {y0.im.x, y1.im.x, y0.im.y, y1.im.y};
+        __half2 hr[4], hm[4];
+        uint32_t vre[4], vim[4];
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+            hr[f] = __floats2half2_rn(yr[f], yi[f]);
+            hm[f] = __floats2half2_rn(yi[f], -yr[f]);
+            vre[f] = h2u(hr[f]);
+            vim[f] = h2u(hm[f]);
+        }
+        const int off_re = core_off<C::SBO>(2 * t, quad), off_im = core_off<C::SBO>(2 * t + 1, quad);
+        *reinterpret_cast<uint4*>(bhi + off_re) = make_uint4(vre[0], vre[1], vre[2], vre[3]);
+        *reinterpret_cast<uint4*>(bhi + off_im) = make_uint4(vim[0], vim[1], vim[2], vim[3]);
+        if constexpr (C::B_LO) {
+#pragma unroll
+            for (int f = 0; f < 4; ++f) {
+                const float2 back = __half22float2(hr[f]);
+                const float lr = yr[f] - back.x, li = yi[f] - back.y;
+                vre[f] = h2u(__floats2half2_rn(lr, li));
+                vim[f] = h2u(__floats2half2_rn(li, -lr));
+            }
+            *reinterpret_cast<uint4*>(blo + off_re) = make_uint4(vre[0], vre[1], vre[2], vre[3]);
+            *reinterpret_cast<uint4*>(blo + off_im) = make_uint4(vim[0], vim[1], vim[2], vim[3]);
+        }
+    }
+}
+
+// MODE: 0 = detect and integrate, 1 = dump up-channelised voltages,
+//       2 = dump the N-S/E-W beams of the GEMM (stage dump).
+template <int TERMS, int MODE>
+__global__ void __launch_bounds__(kTcThreads, 1) fused_tc_kernel(const __grid_constant__ Batch bt) {
+    using C = TcCfg<TERMS>;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ uint32_t tmem_base_s;
+    __shared__ int abort_s;
+    unsigned char* stage_base = smem;
+    float4* tw_s = reinterpret_cast<float4*>(smem + 2 * C::STAGE);
+    uint64_t* mbar_s = reinterpret_cast<uint64_t*>(smem + 2 * C::STAGE + 8 * 8 * 16);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int ell = 32 * (warp & 3) + lane;
+    const int hh = warp >> 2;
+    const int m = ell + 128 * hh;
+    const uint32_t smem0 = static_cast<uint32_t>(__cvta_generic_to_shared(smem));
+    const uint32_t mbar0 = static_cast<uint32_t>(__cvta_generic_to_shared(&mbar_s[0]));
+    const uint32_t mbar1 = static_cast<uint32_t>(__cvta_generic_to_shared(&mbar_s[1]));
+
+    if (warp == 0) {
+        const uint32_t dst = static_cast<uint32_t>(__cvta_generic_to_shared(&tmem_base_s));
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" :: "r"(dst) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(mbar0) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(mbar1) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        abort_s = 0;
+    }
+    for (int i = tid; i < 64; i += kTcThreads) {
+        const int it = i >> 3, c = i & 7;
+        const float2 w0 = bt.tw128[(2 * it * c) & (kUp - 1)];
+        const float2 w1 = bt.tw128[((2 * it + 1) * c) & (kUp - 1)];
+        tw_s[i] = make_float4(w0.x, w1.x, w0.y, w1.y);
+    }
+    cta_sync();
+    const uint32_t tmem = tmem_base_s;
+    const uint32_t tlane = tmem + (static_cast<uint32_t>(32 * (warp & 3)) << 16);
+    uint32_t ph0 = 0, ph1 = 0;
+    bool ok = true;
+
+    for (int item = blockIdx.x; item < bt.n_items && ok; item += gridDim.x) {
+        int sgi = 0;
+        while (sgi + 1 < bt.n_segs && bt.segs[sgi + 1].item_begin <= item) ++sgi;
+        const Seg& sg = bt.segs[sgi];
+        const int local = item - sg.item_begin;
+        const int F = local >> 2, j = local & 3;
+        EwW w;
+        load_ew(bt.ew, sg.table, j, w);
+        const unsigned char* a_hi = bt.a_tc + (size_t)sg.table * bt.a_tc_stride;
+        const unsigned char* a_lo = a_hi + (size_t)C::NCH * C::OPER;
+
+        float2 acc[kSub];
+#pragma unroll
+        for (int s = 0; s < kSub; ++s) acc[s] = make_float2(0.f, 0.f);
+
+        for (int ps = 0; ps < kTds * kPol && ok; ++ps) {
+            const int blk = ps >> 1, pol = ps & 1;
+            const uint32_t sel = 0x4400u | ((2u + pol) << 4) | (uint32_t)pol;
+            const long long row0 = (long long)F * kFrame + blk * kUp;
+            for (int kc = 0; kc < C::NCH; ++kc) {
+                const int s = kc & 1;
+                if (kc >= 2) {
+                    if (!mbar_wait(s ? mbar1 : mbar0, s ? ph1 : ph0)) ok = false;
+                    if (s) ph1 ^= 1; else ph0 ^= 1;
+                }
+                unsigned char* st = stage_base + s * C::STAGE;
+                unsigned char* sa_hi = st;
+                unsigned char* sa_lo = st + C::OPER;
+                unsigned char* sb_hi = st + (C::A_LO ? 2 : 1) * C::OPER;
+                unsigned char* sb_lo = sb_hi + C::OPER;
+                produce_b<TERMS>(sg, row0, kc, sel, w, sb_hi, sb_lo, tid);
+                {
+                    const uint4* src = reinterpret_cast<const uint4*>(a_hi + (size_t)kc * C::OPER);
+                    uint4* dst = reinterpret_cast<uint4*>(sa_hi);
+                    for (int i = tid; i < C::OPER / 16; i += kTcThreads) dst[i] = __ldg(src + i);
+                    if constexpr (C::A_LO) {
+                        const uint4* src2 = reinterpret_cast<const uint4*>(a_lo + (size_t)kc * C::OPER);
+                        uint4* dst2 = reinterpret_cast<uint4*>(sa_lo);
+                        for (int i = tid; i < C::OPER / 16; i += kTcThreads) dst2[i] = __ldg(src2 + i);
+                    }
+                }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                if (!ok) abort_s = 1;
+                cta_sync();
+                if (abort_s) {
+                    ok = false;
+                    break;
+                }
+                if (tid == 0) {
+                    const uint32_t ahi = smem0 + (uint32_t)(sa_hi - smem), alo = smem0 + (uint32_t)(sa_lo - smem);
+                    const uint32_t bhi = smem0 + (uint32_t)(sb_hi - smem), blo = smem0 + (uint32_t)(sb_lo - smem);
+#pragma unroll
+                    for (int ks = 0; ks < C::KC / 16; ++ks) {
+#pragma unroll
+                        for (int mt = 0; mt < 2; ++mt) {
+                            const uint32_t d = tmem + mt * 256;
+                            const uint32_t aoff = mt * 16 * C::SBO + ks * 256;
+                            const uint64_t da = smem_desc(ahi + aoff, 128, C::SBO);
+                            const uint64_t db = smem_desc(bhi + ks * 256, 128, C::SBO);
+                            mma_f16(d, da, db, (kc | ks) ? 1u : 0u);
+                            if constexpr (C::B_LO)
+                                mma_f16(d, da, smem_desc(blo + ks * 256, 128, C::SBO), 1u);
+                            if constexpr (C::A_LO)
+                                mma_f16(d, smem_desc(alo + aoff, 128, C::SBO), db, 1u);
+                        }
+                    }
+                    mma_commit(s ? mbar1 : mbar0);
+                }
+            }
+            if (!ok) break;
+            // the last two commits cover every MMA of the pass
+            if (!mbar_wait(mbar0, ph0)) ok = false;
+            ph0 ^= 1;
+            if (!mbar_wait(mbar1, ph1)) ok = false;
+            ph1 ^= 1;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            if (!ok) break;
+
+            if constexpr (MODE == 2) {
+                // stage dump: X for bin m, times 0..127 of this block
+                float2* d = bt.dump + ((((long long)(F * kTds + blk) * kPol + pol) * kEw + j) * kNs + m) * kUp;
+                for (int c4 = 0; c4 < 4; ++c4) {
+                    cp y[16];
+                    tmem_ld64(tlane + hh * 256 + 64 * c4, y);
+#pragma unroll
+                    for (int b = 0; b < 16; ++b) {
+                        d[32 * c4 + b] = make_float2(y[b].re.x, y[b].im.x);
+                        d[32 * c4 + 16 + b] = make_float2(y[b].re.y, y[b].im.y);
+                    }
+                }
+            } else {
+                // first up-channel pass, in place: 8-point DFT over a (t = 16 a + b) per residue pair
+#pragma unroll 1
+                for (int bp = 0; bp < 8; ++bp) {
+                    const int b0 = 2 * bp;
+                    cp z[8];
+                    tmem_ld8x4(tlane + hh * 256 + 2 * b0, z);
+                    dft8(z);
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) {
+                        if (c) {
+                            const float4 tw = tw_s[bp * 8 + c];
+                            z[c] = cmulp(z[c], make_float2(tw.x, tw.y), make_float2(tw.z, tw.w));
+                        }
+                        tmem_st4(tlane + hh * 256 + 2 * (16 * c + b0), z[c].re.x, z[c].im.x, z[c].re.y, z[c].im.y);
+                    }
+                }
+                tmem_wait_st();
+                upchan_pass2(tlane, hh, acc,
+                             MODE == 1
+                                 ? bt.dump + ((((long long)(F * kTds + blk) * kPol + pol) * kEw + j) * kNs + m) * kUp
+                                 : nullptr);
+            }
+            // the next pass's MMAs are issued after a CTA barrier that orders them after these loads
+        }
+
+        if constexpr (MODE == 0) {
+            if (ok) {
+                float* o = sg.out + (long long)(kNs * j + m) * sg.beam_stride + F;
+#pragma unroll
+                for (int s = 0; s < kSub; ++s) o[(long long)s * sg.sub_stride] = acc[s].x + acc[s].y;
+            }
+        }
+    }
+
+    if (!ok && bt.status) atomicExch(bt.status, 1);
+    cta_sync();
+    if (warp == 0) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" :: "r"(tmem) : "memory");
+    }
+}
+
+template <int TERMS, int MODE>
+cudaError_t launch_tc(const Batch& b, int grid, cudaStream_t s) {
+    if (b.n_items <= 0) return cudaSuccess;
+    const int smem = (int)TcCfg<TERMS>::SMEM;
+    cudaError_t e = cudaFuncSetAttribute(fused_tc_kernel<TERMS, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    fused_tc_kernel<TERMS, MODE><<<grid, kTcThreads, smem, s>>>(b);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t tc_a_bytes(int terms) {
+    const size_t one = (size_t)kNs * 2 * kFeed * 2;              // 256 rows x 512 K x FP16
+    return terms == 3 ? 2 * one : one;
+}
+
+int tc_chunk_k(int terms) { return terms == 3 ? TcCfg<3>::KC : TcCfg<1>::KC; }
+
+cudaError_t fused_tc_launch(const Batch& b, int terms, int mode, int grid, cudaStream_t s) {
+    switch (terms * 10 + mode) {
+        case 10: return launch_tc<1, 0>(b, grid, s);
+        case 11: return launch_tc<1, 1>(b, grid, s);
+        case 12: return launch_tc<1, 2>(b, grid, s);
+        case 20: return launch_tc<2, 0>(b, grid, s);
+        case 21: return launch_tc<2, 1>(b, grid, s);
+        case 22: return launch_tc<2, 2>(b, grid, s);
+        case 30: return launch_tc<3, 0>(b, grid, s);
+        case 31: return launch_tc<3, 1>(b, grid, s);
+        case 32: return launch_tc<3, 2>(b, grid, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace chimebf

@@ -9,6 +9,7 @@
 #include "../../include/chimebf.h"
 #include "bf_internal.h"
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -33,6 +34,7 @@ namespace {
 constexpr double kC0 = 299792458.0;
 constexpr double kPi = 3.14159265358979323846;
 constexpr int kTableCap = 4096;
+constexpr int kTcTableCap = 512;       // tensor-core twiddle images held at once
 constexpr int kMaxInflight = 4;
 
 thread_local std::string g_err;
@@ -100,6 +102,10 @@ struct bf_plan_s {
     float2* d_tw512 = nullptr;
     float2* d_tw128 = nullptr;
     std::map<uint64_t, int> table_of_freq;   // key: bit pattern of the double
+    int terms = 0;                            // tensor-core GEMM terms (0: FP32 FFT form)
+    unsigned char* d_atc = nullptr;           // [kTcTableCap][tc_a_bytes(terms)] FP16 twiddle images
+    int* h_status = nullptr;                  // mapped status word written by kernels
+    int* d_status = nullptr;
 
     std::mutex mu;
     std::condition_variable cv;
@@ -160,6 +166,33 @@ void ew_table(const bf_plan_s* p, double f, float* ew) {
         }
 }
 
+// Tensor-core twiddle image of one frequency: A[m][2n] = cos, A[m][2n+1] = sin
+// of 2 pi n L(m) / 512 (the clamped rows of the zero-padded DFT, Eq. 1), FP16
+// hi (and lo = A - hi), laid out chunk by chunk exactly as the kernel's shared
+// memory operand: 8-row x 16-byte core matrices, k-groups 128 B apart, row
+// groups KC/8 * 128 B apart.
+void tc_image(int terms, const int32_t* lut, std::vector<__half>& img) {
+    const int KC = tc_chunk_k(terms);
+    const size_t oper = (size_t)kNs * KC;                 // halves per chunk
+    const size_t nch = 2 * kFeed / KC;
+    const size_t one = oper * nch;
+    img.assign(terms == 3 ? 2 * one : one, __float2half(0.f));
+    for (int m = 0; m < kNs; ++m)
+        for (int n = 0; n < kFeed; ++n) {
+            const long long e = ((long long)n * lut[m]) % kBins;
+            const double th = 2.0 * kPi * (double)e / kBins;
+            const double v[2] = {std::cos(th), std::sin(th)};
+            for (int c = 0; c < 2; ++c) {
+                const int kg = 2 * n + c;
+                const size_t kc = kg / KC, k = kg % KC;
+                const size_t off = kc * oper + ((size_t)(m >> 3) * (KC / 8) + (k >> 3)) * 64 + (m & 7) * 8 + (k & 7);
+                const __half hi = __double2half(v[c]);
+                img[off] = hi;
+                if (terms == 3) img[one + off] = __double2half(v[c] - (double)__half2float(hi));
+            }
+        }
+}
+
 uint64_t freq_key(double f) {
     uint64_t k;
     std::memcpy(&k, &f, sizeof k);
@@ -183,6 +216,14 @@ int table_for(bf_plan_s* p, double f, int* idx) {
     ew_table(p, f, ew);
     CK(cudaMemcpy(p->d_lut + (size_t)n * kNs, lut16, sizeof lut16, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(p->d_ew + (size_t)n * kEw * kCyl, ew, sizeof ew, cudaMemcpyHostToDevice));
+    if (p->terms) {
+        if (n >= kTcTableCap) return fail(BF_ENOMEM, "too many distinct channel frequencies for the tensor-core form");
+        if (!p->d_atc) CK(cudaMalloc(&p->d_atc, (size_t)kTcTableCap * tc_a_bytes(p->terms)));
+        std::vector<__half> img;
+        tc_image(p->terms, lut, img);
+        CK(cudaMemcpy(p->d_atc + (size_t)n * tc_a_bytes(p->terms), img.data(), img.size() * sizeof(__half),
+                      cudaMemcpyHostToDevice));
+    }
     p->table_of_freq[freq_key(f)] = n;
     *idx = n;
     return BF_OK;
@@ -195,6 +236,9 @@ Batch make_batch(const bf_plan_s* p) {
     b.ew = p->d_ew;
     b.tw512 = p->d_tw512;
     b.tw128 = p->d_tw128;
+    b.a_tc = p->d_atc;
+    b.a_tc_stride = p->terms ? tc_a_bytes(p->terms) : 0;
+    b.status = p->d_status;
     return b;
 }
 
@@ -308,7 +352,9 @@ int launch_jobs(bf_plan_s* p, std::vector<Job>& jobs, size_t bytes) {
     }
     if (b.n_segs) batches.push_back(b);
     for (auto& bb : batches) {
-        cudaError_t e = fused_fp32_launch(bb, std::min(p->grid, bb.n_items), p->stream);
+        bb.a_tc = p->d_atc;                       // tables may have been created above
+        cudaError_t e = p->terms ? fused_tc_launch(bb, p->terms, 0, std::min(p->grid, bb.n_items), p->stream)
+                                 : fused_fp32_launch(bb, std::min(p->grid, bb.n_items), p->stream);
         if (e != cudaSuccess) return cuda_fail(e, "fused kernel launch");
     }
     for (auto& c : carries) {
@@ -365,10 +411,16 @@ bool retire(bf_plan_s* p) {
         InflightBatch& ib = p->inflight.front();
         cudaError_t e = cudaEventQuery(ib.ev);
         if (e == cudaErrorNotReady) break;
+        const bool expired = p->h_status && *(volatile int*)p->h_status != 0;
+        if (expired) *(volatile int*)p->h_status = 0;
         for (uint64_t t : ib.tickets) {
             auto it = p->tickets.find(t);
             if (it == p->tickets.end()) continue;
-            if (e == cudaSuccess) {
+            if (e == cudaSuccess && expired) {
+                it->second.state = T_ERROR;
+                it->second.err = BF_ETIMEDOUT;
+                it->second.msg = "a bounded device-side wait expired; the batch's output is incomplete";
+            } else if (e == cudaSuccess) {
                 it->second.state = T_DONE;
             } else {
                 it->second.state = T_ERROR;
@@ -477,12 +529,17 @@ int bf_plan(const bf_config* cfg, bf_plan_t* out) {
     if (!(cfg->feed_spacing_m > 0) || !(cfg->cyl_spacing_m >= 0) || !std::isfinite(cfg->feed_spacing_m) ||
         !std::isfinite(cfg->cyl_spacing_m))
         return fail(BF_EINVAL, "bad spacings");
-    if (cfg->form != BF_FP32_FFT) return fail(BF_EINVAL, "form not available in this build");
+    if (cfg->form == BF_TC_DFT512)
+        return fail(BF_EINVAL, "BF_TC_DFT512 is not built: its result equals BF_TC_DFT256 at twice the GEMM work");
+    if (cfg->form != BF_FP32_FFT && cfg->form != BF_TC_DFT256 && cfg->form != BF_TC_DFT256_X2 &&
+        cfg->form != BF_TC_DFT256_X1)
+        return fail(BF_EINVAL, "unknown form");
     if (cfg->mode != BF_MODE_DIRECT && cfg->mode != BF_MODE_SERVING) return fail(BF_EINVAL, "bad mode");
     if (cfg->max_streams < 0) return fail(BF_EINVAL, "negative max_streams");
 
     std::unique_ptr<bf_plan_s> p(new bf_plan_s);
     p->cfg = *cfg;
+    p->terms = cfg->form == BF_TC_DFT256 ? 3 : cfg->form == BF_TC_DFT256_X2 ? 2 : cfg->form == BF_TC_DFT256_X1 ? 1 : 0;
     p->ns_sin.resize(kNs);
     p->ew_sin.resize(kEw);
     int prc = fill_pointings(p.get(), cfg);
@@ -522,6 +579,9 @@ int bf_plan(const bf_config* cfg, bf_plan_t* out) {
     for (int e = 0; e < kUp; ++e)
         tw[e] = make_float2((float)std::cos(-2.0 * kPi * e / kUp), (float)std::sin(-2.0 * kPi * e / kUp));
     CK(cudaMemcpy(p->d_tw128, tw.data(), kUp * sizeof(float2), cudaMemcpyHostToDevice));
+    CK(cudaHostAlloc(&p->h_status, sizeof(int), cudaHostAllocMapped));
+    *p->h_status = 0;
+    CK(cudaHostGetDevicePointer(&p->d_status, p->h_status, 0));
 
     if (p->cfg.mode == BF_MODE_SERVING) {
         bf_plan_s* raw = p.get();
@@ -645,6 +705,8 @@ int bf_destroy(bf_plan_t p) {
     cudaFree(p->d_ew);
     cudaFree(p->d_tw512);
     cudaFree(p->d_tw128);
+    if (p->d_atc) cudaFree(p->d_atc);
+    if (p->h_status) cudaFreeHost(p->h_status);
     if (p->own_stream) cudaStreamDestroy(p->stream);
     delete p;
     return rc;
@@ -690,10 +752,12 @@ int bf_debug_beams(bf_plan_t p, double freq_hz, const uint8_t* d_vin, int64_t n_
     return BF_OK;
 }
 
-int bf_debug_upchan(bf_plan_t p, double freq_hz, const uint8_t* d_vin, int64_t n_samples, float* d_out) {
+static int debug_fused(bf_plan_t p, double freq_hz, const uint8_t* d_vin, int64_t n_samples, float* d_out,
+                       int mode) {
     if (!p || n_samples < 0 || n_samples % kFrame != 0 || !(freq_hz > 0) || (n_samples > 0 && (!d_vin || !d_out)))
         return fail(BF_EINVAL, "bad argument (n_samples must be a multiple of 384)");
     if (((uintptr_t)d_vin & 15) != 0) return fail(BF_EINVAL, "vin must be 16-byte aligned");
+    if (mode == 2 && !p->terms) return fail(BF_EINVAL, "the GEMM dump needs a tensor-core form");
     CK(cudaSetDevice(p->device));
     Batch b = make_batch(p);
     {
@@ -701,15 +765,33 @@ int bf_debug_upchan(bf_plan_t p, double freq_hz, const uint8_t* d_vin, int64_t n
         int rc = table_for(p, freq_hz, &b.segs[0].table);
         if (rc) return rc;
     }
+    b.a_tc = p->d_atc;
     const int nf = (int)(n_samples / kFrame);
     b.n_segs = 1;
     b.n_items = nf * kEw;
     b.segs[0].vin = d_vin;
     b.segs[0].n_frames = nf;
     b.dump = reinterpret_cast<float2*>(d_out);
-    CK(fused_fp32_dump_launch(b, std::min(p->grid, std::max(b.n_items, 1)), p->stream));
+    const int grid = std::min(p->grid, std::max(b.n_items, 1));
+    if (p->terms) {
+        CK(fused_tc_launch(b, p->terms, mode, grid, p->stream));
+    } else {
+        CK(fused_fp32_dump_launch(b, grid, p->stream));
+    }
     CK(cudaStreamSynchronize(p->stream));
+    if (p->h_status && *(volatile int*)p->h_status) {
+        *(volatile int*)p->h_status = 0;
+        return fail(BF_ETIMEDOUT, "a bounded device-side wait expired");
+    }
     return BF_OK;
+}
+
+int bf_debug_upchan(bf_plan_t p, double freq_hz, const uint8_t* d_vin, int64_t n_samples, float* d_out) {
+    return debug_fused(p, freq_hz, d_vin, n_samples, d_out, 1);
+}
+
+int bf_debug_gemm(bf_plan_t p, double freq_hz, const uint8_t* d_vin, int64_t n_samples, float* d_out) {
+    return debug_fused(p, freq_hz, d_vin, n_samples, d_out, 2);
 }
 
 }  // extern "C"
