@@ -11,20 +11,23 @@
 // with y_j the E-W phased feed line (Sec. 3) of block time t.  As a real GEMM:
 // rows = bins m (two M = 128 tiles), columns = (t, re/im) (N = 256), K = (n,
 // re/im) = 512.  With A[m][2n] = cos, A[m][2n+1] = sin (of 2 pi n L / 512) the
-// column (t, 0) of B holds (yr, yi) and (t, 1) holds (yi, -yr), so the two
-// columns give Re and Im of X with one A.  The accumulator lands in tensor
-// memory exactly where the up-channel passes want it: lane = bin (m, m+128),
-// column 2t / 2t+1 = Re / Im of time t.
+// column t of B holds (yr, yi) and column 128 + t holds (yi, -yr), so the two
+// halves give Re and Im of X with one A.  The accumulator lands in tensor
+// memory where the up-channel passes read it: lane = bin (m, m + 128), columns
+// [0, 128) = Re X(t), [128, 256) = Im X(t) of each 256-column bin half.
 //
 // Precision: FP16 operands, FP32 accumulation.  y is split y = y_hi + y_lo in
 // FP16 (22 bits together); the twiddles are FP16 (hi) and, for three terms,
 // also lo.  Terms: 1 = A_hi y_hi, 2 = + A_hi y_lo, 3 = + A_lo y_hi.
 //
-// Pipeline per pass: K is streamed in chunks through two shared-memory stages;
-// all warps build the B chunk (unpack, E-W, FP16 split) and copy the A chunk,
-// one thread issues the MMAs and commits them to the stage's mbarrier, which
-// the producers wait on before reusing the stage.  Every wait is bounded by
-// %globaltimer; on expiry the kernel records an error and leaves cleanly.
+// Pipeline per pass: K is streamed in chunks through two shared-memory stages.
+// Thread 0 starts the bulk copy (TMA engine) of each twiddle chunk one chunk
+// ahead; all warps build the B chunk (unpack, E-W, FP16 split) from raw bytes
+// prefetched into registers one chunk ahead and arrive on the stage's "B full"
+// mbarrier; thread 0 waits for B and twiddles, issues the MMAs and commits
+// them to the stage's "empty" mbarrier, which the producers wait on before
+// reusing the stage.  No CTA barrier sits inside the chunk loop.  Every wait is
+// bounded by %globaltimer; on expiry the kernel records an error and leaves.
 #include "device_common.cuh"
 
 #include <cuda_fp16.h>
@@ -47,7 +50,8 @@ struct TcCfg {
     static constexpr bool A_LO = TERMS == 3;
     static constexpr bool B_LO = TERMS >= 2;
     static constexpr int STAGE = OPER * (1 + (A_LO ? 1 : 0) + 1 + (B_LO ? 1 : 0));
-    static constexpr size_t SMEM = 2ull * STAGE + 8 * 8 * 16 + 64;   // + up-channel twiddles + barriers
+    static constexpr int NOCT = KC / 16;                          // 8-feed octets per chunk
+    static constexpr size_t SMEM = 2ull * STAGE + 8 * 8 * 16 + 64;   // + up-channel twiddles + 6 barriers
 };
 
 // Byte offset of element (row r, k) in a K-major operand chunk without
@@ -101,97 +105,221 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
     }
 }
 
-// Eight 4-column TMEM loads (columns base + 32 a .. + 3, a = 0..7) -> SoA pairs.
-__device__ __forceinline__ void tmem_ld8x4(uint32_t taddr, cp (&z)[8]) {
+// TMEM access for the split Re/Im layout: 16 two-column loads (Re at base +
+// 16 a + b0, Im at base + 128 + 16 a + b0, a = 0..7) -> SoA pairs (b0, b0 + 1).
+__device__ __forceinline__ void tmem_ld_p1(uint32_t base, cp (&z)[8]) {
     uint32_t r[32];
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%32];\n\t"
-        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%4, %5, %6, %7}, [%33];\n\t"
-        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%8, %9, %10, %11}, [%34];\n\t"
-        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%12, %13, %14, %15}, [%35];\n\t"
-        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%16, %17, %18, %19}, [%36];\n\t"
-        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%20, %21, %22, %23}, [%37];\n\t"
-        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%24, %25, %26, %27}, [%38];\n\t"
-        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%28, %29, %30, %31}, [%39];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0, %1}, [%32];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%2, %3}, [%33];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%4, %5}, [%34];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%6, %7}, [%35];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%8, %9}, [%36];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%10, %11}, [%37];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%12, %13}, [%38];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%14, %15}, [%39];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%16, %17}, [%40];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%18, %19}, [%41];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%20, %21}, [%42];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%22, %23}, [%43];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%24, %25}, [%44];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%26, %27}, [%45];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%28, %29}, [%46];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%30, %31}, [%47];\n\t"
         "tcgen05.wait::ld.sync.aligned;"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
           "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
           "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
           "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr), "r"(taddr + 32), "r"(taddr + 64), "r"(taddr + 96), "r"(taddr + 128), "r"(taddr + 160),
-          "r"(taddr + 192), "r"(taddr + 224)
+        : "r"(base), "r"(base + 16), "r"(base + 32), "r"(base + 48), "r"(base + 64), "r"(base + 80),
+          "r"(base + 96), "r"(base + 112), "r"(base + 128), "r"(base + 144), "r"(base + 160), "r"(base + 176),
+          "r"(base + 192), "r"(base + 208), "r"(base + 224), "r"(base + 240)
         : "memory");
 #pragma unroll
     for (int a = 0; a < 8; ++a) {
-        z[a].re = make_float2(__uint_as_float(r[4 * a]), __uint_as_float(r[4 * a + 2]));
-        z[a].im = make_float2(__uint_as_float(r[4 * a + 1]), __uint_as_float(r[4 * a + 3]));
+        z[a].re = make_float2(__uint_as_float(r[2 * a]), __uint_as_float(r[2 * a + 1]));
+        z[a].im = make_float2(__uint_as_float(r[16 + 2 * a]), __uint_as_float(r[16 + 2 * a + 1]));
+    }
+}
+
+__device__ __forceinline__ void tmem_st2(uint32_t taddr, float a, float b) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x2.b32 [%0], {%1, %2};"
+                 :: "r"(taddr), "r"(__float_as_uint(a)), "r"(__float_as_uint(b)) : "memory");
+}
+
+// 32 consecutive columns -> 32 floats
+__device__ __forceinline__ void tmem_ld32f(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// First up-channel pass in place on the split layout (t = 16 a + b): 8-point
+// DFT over a for the residue pair (b0, b0 + 1), twiddled by exp(-2 pi i b c / 128).
+__device__ __forceinline__ void upchan_pass1_split(uint32_t base, const float4* tw_s) {
+#pragma unroll 1
+    for (int bp = 0; bp < 8; ++bp) {
+        const int b0 = 2 * bp;
+        cp z[8];
+        tmem_ld_p1(base + b0, z);
+        dft8(z);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            if (c) {
+                const float4 tw = tw_s[bp * 8 + c];
+                z[c] = cmulp(z[c], make_float2(tw.x, tw.y), make_float2(tw.z, tw.w));
+            }
+            tmem_st2(base + 16 * c + b0, z[c].re.x, z[c].re.y);
+            tmem_st2(base + 128 + 16 * c + b0, z[c].im.x, z[c].im.y);
+        }
+    }
+}
+
+// Second pass on the split layout: Re of (c, b) at 16 c + b, Im at 128 + 16 c + b.
+__device__ __forceinline__ void upchan_pass2_split(uint32_t base, float2 (&acc)[kSub], float2* dump) {
+#pragma unroll 1
+    for (int cpi = 0; cpi < 4; ++cpi) {
+        float re[32], im[32];
+        tmem_ld32f(base + 32 * cpi, re);
+        tmem_ld32f(base + 128 + 32 * cpi, im);
+        cp y[16];
+#pragma unroll
+        for (int b = 0; b < 16; ++b) {
+            y[b].re = make_float2(re[b], re[16 + b]);
+            y[b].im = make_float2(im[b], im[16 + b]);
+        }
+        dft16(y);
+        if (dump) {
+#pragma unroll
+            for (int dd = 0; dd < 16; ++dd) {
+                const int c0 = 2 * cpi;
+                dump[(c0 + 8 * dd + kUp / 2) & (kUp - 1)] = make_float2(y[dd].re.x, y[dd].im.x);
+                dump[(c0 + 1 + 8 * dd + kUp / 2) & (kUp - 1)] = make_float2(y[dd].re.y, y[dd].im.y);
+            }
+        } else {
+#pragma unroll
+            for (int dd = 0; dd < 16; ++dd) {
+                const float2 p = fma2(y[dd].im, y[dd].im, mul2(y[dd].re, y[dd].re));
+                acc[(dd + 8) & 15] = add2(acc[(dd + 8) & 15], p);
+            }
+        }
     }
 }
 
 __device__ __forceinline__ uint32_t h2u(__half2 h) { return *reinterpret_cast<uint32_t*>(&h); }
 
-// Build the B chunk `kc` of pass (blk, pol) for tasks (t, quad) of this thread:
-// unpack 4 feeds x 4 cylinders, E-W toward beam j, split into FP16 hi (+ lo),
-// and store rows (t, re-col) = (yr, yi) and (t, im-col) = (yi, -yr).
+// Producer tasks (t, octet): 8 feeds x 2 pols of every cylinder, one 16-byte
+// load each.  Lanes run over t so the B stores of a quarter warp fill one
+// 128-byte line.
 template <int TERMS>
-__device__ __forceinline__ void produce_b(const Seg& sg, long long row0, int kc, uint32_t sel, const EwW& w,
-                                          unsigned char* bhi, unsigned char* blo, int tid) {
+struct RawB {
+    static constexpr int TASKS = kUp * TcCfg<TERMS>::NOCT / kTcThreads;   // 2 (KC 64) or 1 (KC 32)
+    uint4 v[TASKS][kCyl];
+};
+
+template <int TERMS>
+__device__ __forceinline__ void task_of(int tid, int i, int& t, int& oct) {
     using C = TcCfg<TERMS>;
-    constexpr int TASKS = kUp * C::NQUAD / kTcThreads;       // 4 (KC 64) or 2 (KC 32)
-    const int quad = (tid >> 5) % C::NQUAD;
-    const int tbase = (tid & 31) + 32 * ((tid >> 5) / C::NQUAD);
-    const int n0 = (C::KC / 2) * kc + 4 * quad;             // first feed of the quad
+    oct = (tid >> 5) % C::NOCT;
+    t = (tid & 31) + 32 * ((tid >> 5) / C::NOCT) + i * (kTcThreads / C::NOCT);
+}
+
+template <int TERMS>
+__device__ __forceinline__ void load_b(const Seg& sg, long long row0, int kc, int tid, RawB<TERMS>& r) {
+    using C = TcCfg<TERMS>;
 #pragma unroll
-    for (int i = 0; i < TASKS; ++i) {
-        const int t = tbase + i * (kTcThreads / C::NQUAD);
+    for (int i = 0; i < RawB<TERMS>::TASKS; ++i) {
+        int t, oct;
+        task_of<TERMS>(tid, i, t, oct);
+        const int n0 = (C::KC / 2) * kc + 8 * oct;
         const uint8_t* rp = frame_row(sg, row0 + t) + 2 * n0;
-        uint2 in[kCyl];
 #pragma unroll
-        for (int c = 0; c < kCyl; ++c) in[c] = __ldg(reinterpret_cast<const uint2*>(rp + c * (kFeed * kPol)));
-        // SoA pairs: P0 = feeds (n0, n0 + 2), P1 = feeds (n0 + 1, n0 + 3)
-        cp y0, y1;
+        for (int c = 0; c < kCyl; ++c) r.v[i][c] = __ldg(reinterpret_cast<const uint4*>(rp + c * (kFeed * kPol)));
+    }
+}
+
+// Build the B chunk: unpack, E-W toward beam j, split into FP16 hi (+ lo), and
+// store row t = (yr, yi) per feed and row 128 + t = (yi, -yr).
+template <int TERMS>
+__device__ __forceinline__ void build_b(const RawB<TERMS>& r, uint32_t sel, const EwW& w, unsigned char* bhi,
+                                        unsigned char* blo, int tid) {
+    using C = TcCfg<TERMS>;
 #pragma unroll
-        for (int c = 0; c < kCyl; ++c) {
-            const uint32_t g0 = __byte_perm(in[c].x, 0u, sel), g1 = __byte_perm(in[c].y, 0u, sel);
-            const float2 xi0 = nib2<0>(g0, g1), xr0 = nib2<1>(g0, g1);
-            const float2 xi1 = nib2<2>(g0, g1), xr1 = nib2<3>(g0, g1);
-            if (c == 0) {
-                y0 = {xr0, xi0};
-                y1 = {xr1, xi1};
-            } else {
-                y0.re = fma2(xi0, w.NI[c - 1], fma2(xr0, w.R[c - 1], y0.re));
-                y0.im = fma2(xr0, w.I[c - 1], fma2(xi0, w.R[c - 1], y0.im));
-                y1.re = fma2(xi1, w.NI[c - 1], fma2(xr1, w.R[c - 1], y1.re));
-                y1.im = fma2(xr1, w.I[c - 1], fma2(xi1, w.R[c - 1], y1.im));
+    for (int i = 0; i < RawB<TERMS>::TASKS; ++i) {
+        int t, oct;
+        task_of<TERMS>(tid, i, t, oct);
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {           // feeds 4 half .. 4 half + 3 of the octet
+            cp y0, y1;                                    // SoA: (n, n + 2) and (n + 1, n + 3)
+#pragma unroll
+            for (int c = 0; c < kCyl; ++c) {
+                const uint32_t w0 = half ? r.v[i][c].z : r.v[i][c].x, w1 = half ? r.v[i][c].w : r.v[i][c].y;
+                const uint32_t g0 = __byte_perm(w0, 0u, sel), g1 = __byte_perm(w1, 0u, sel);
+                const float2 xi0 = nib2<0>(g0, g1), xr0 = nib2<1>(g0, g1);
+                const float2 xi1 = nib2<2>(g0, g1), xr1 = nib2<3>(g0, g1);
+                if (c == 0) {
+                    y0 = {xr0, xi0};
+                    y1 = {xr1, xi1};
+                } else {
+                    y0.re = fma2(xi0, w.NI[c - 1], fma2(xr0, w.R[c - 1], y0.re));
+                    y0.im = fma2(xr0, w.I[c - 1], fma2(xi0, w.R[c - 1], y0.im));
+                    y1.re = fma2(xi1, w.NI[c - 1], fma2(xr1, w.R[c - 1], y1.re));
+                    y1.im = fma2(xr1, w.I[c - 1], fma2(xi1, w.R[c - 1], y1.im));
+                }
             }
-        }
-        // feeds in k order: n0 (y0.x), n0+1 (y1.x), n0+2 (y0.y), n0+3 (y1.y)
-        const float yr[4] = {y0.re.x, y1.re.x, y0.re.y, y1.re.y};
-        const float yi[4] = {y0.im.x, y1.im.x, y0.im.y, y1.im.y};
-        __half2 hr[4], hm[4];
-        uint32_t vre[4], vim[4];
-#pragma unroll
-        for (int f = 0; f < 4; ++f) {
-            hr[f] = __floats2half2_rn(yr[f], yi[f]);
-            hm[f] = __floats2half2_rn(yi[f], -yr[f]);
-            vre[f] = h2u(hr[f]);
-            vim[f] = h2u(hm[f]);
-        }
-        const int off_re = core_off<C::SBO>(2 * t, quad), off_im = core_off<C::SBO>(2 * t + 1, quad);
-        *reinterpret_cast<uint4*>(bhi + off_re) = make_uint4(vre[0], vre[1], vre[2], vre[3]);
-        *reinterpret_cast<uint4*>(bhi + off_im) = make_uint4(vim[0], vim[1], vim[2], vim[3]);
-        if constexpr (C::B_LO) {
+            const float yr[4] = {y0.re.x, y1.re.x, y0.re.y, y1.re.y};
+            const float yi[4] = {y0.im.x, y1.im.x, y0.im.y, y1.im.y};
+            __half2 hr[4];
+            uint32_t vre[4], vim[4];
 #pragma unroll
             for (int f = 0; f < 4; ++f) {
-                const float2 back = __half22float2(hr[f]);
-                const float lr = yr[f] - back.x, li = yi[f] - back.y;
-                vre[f] = h2u(__floats2half2_rn(lr, li));
-                vim[f] = h2u(__floats2half2_rn(li, -lr));
+                hr[f] = __floats2half2_rn(yr[f], yi[f]);
+                vre[f] = h2u(hr[f]);
+                vim[f] = h2u(__floats2half2_rn(yi[f], -yr[f]));
             }
-            *reinterpret_cast<uint4*>(blo + off_re) = make_uint4(vre[0], vre[1], vre[2], vre[3]);
-            *reinterpret_cast<uint4*>(blo + off_im) = make_uint4(vim[0], vim[1], vim[2], vim[3]);
+            const int kg = 2 * oct + half;
+            const int off_re = core_off<C::SBO>(t, kg), off_im = core_off<C::SBO>(128 + t, kg);
+            *reinterpret_cast<uint4*>(bhi + off_re) = make_uint4(vre[0], vre[1], vre[2], vre[3]);
+            *reinterpret_cast<uint4*>(bhi + off_im) = make_uint4(vim[0], vim[1], vim[2], vim[3]);
+            if constexpr (C::B_LO) {
+#pragma unroll
+                for (int f = 0; f < 4; ++f) {
+                    const float2 back = __half22float2(hr[f]);
+                    const float lr = yr[f] - back.x, li = yi[f] - back.y;
+                    vre[f] = h2u(__floats2half2_rn(lr, li));
+                    vim[f] = h2u(__floats2half2_rn(li, -lr));
+                }
+                *reinterpret_cast<uint4*>(blo + off_re) = make_uint4(vre[0], vre[1], vre[2], vre[3]);
+                *reinterpret_cast<uint4*>(blo + off_im) = make_uint4(vim[0], vim[1], vim[2], vim[3]);
+            }
         }
     }
+}
+
+// One-thread bulk copy (TMA engine) of `bytes` into shared memory, completing
+// on an mbarrier that expects that many bytes.
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t mbar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 :: "r"(dst), "l"(src), "r"(bytes), "r"(mbar) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect(uint32_t mbar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(mbar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(mbar) : "memory");
 }
 
 // MODE: 0 = detect and integrate, 1 = dump up-channelised voltages,
@@ -211,8 +339,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) fused_tc_kernel(const __grid_co
     const int hh = warp >> 2;
     const int m = ell + 128 * hh;
     const uint32_t smem0 = static_cast<uint32_t>(__cvta_generic_to_shared(smem));
-    const uint32_t mbar0 = static_cast<uint32_t>(__cvta_generic_to_shared(&mbar_s[0]));
-    const uint32_t mbar1 = static_cast<uint32_t>(__cvta_generic_to_shared(&mbar_s[1]));
+    const uint32_t bar0 = static_cast<uint32_t>(__cvta_generic_to_shared(&mbar_s[0]));
+    auto bar = [&](int i) { return bar0 + 8u * (uint32_t)i; };
+    // barrier i of stage s: empty (0 + s): the stage's MMAs are done; afull (2 + s):
+    // its twiddle chunk landed; bfull (4 + s): all 8 warps stored their part of B
+    auto empty = [&](int s) { return bar0 + 8u * (uint32_t)s; };
+    auto afull = [&](int s) { return bar0 + 8u * (uint32_t)(2 + s); };
+    auto bfull = [&](int s) { return bar0 + 8u * (uint32_t)(4 + s); };
 
     if (warp == 0) {
         const uint32_t dst = static_cast<uint32_t>(__cvta_generic_to_shared(&tmem_base_s));
@@ -220,8 +353,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) fused_tc_kernel(const __grid_co
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(mbar0) : "memory");
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(mbar1) : "memory");
+        for (int i = 0; i < 4; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(bar(i)) : "memory");
+        for (int i = 4; i < 6; ++i)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(bar(i)), "r"(kTcThreads / 32) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         abort_s = 0;
     }
@@ -233,9 +367,20 @@ __global__ void __launch_bounds__(kTcThreads, 1) fused_tc_kernel(const __grid_co
     }
     cta_sync();
     const uint32_t tmem = tmem_base_s;
-    const uint32_t tlane = tmem + (static_cast<uint32_t>(32 * (warp & 3)) << 16);
-    uint32_t ph0 = 0, ph1 = 0;
+    const uint32_t tlane = tmem + (static_cast<uint32_t>(32 * (warp & 3)) << 16) + hh * 256;
+    // phase parities, one bit per stage (pa, pb: thread 0 only)
+    uint32_t pe = 0, pa = 0, pb = 0;
+    auto par = [](uint32_t bits, int s) { return (bits >> s) & 1u; };
     bool ok = true;
+
+    // Thread 0: bulk-copy twiddle chunk kc of table image `a` into stage s.
+    auto issue_a = [&](const unsigned char* a_hi, const unsigned char* a_lo, int kc, int s) {
+        unsigned char* st = stage_base + s * C::STAGE;
+        mbar_expect(afull(s), (C::A_LO ? 2 : 1) * C::OPER);
+        bulk_g2s(smem0 + (uint32_t)(st - smem), a_hi + (size_t)kc * C::OPER, C::OPER, afull(s));
+        if constexpr (C::A_LO)
+            bulk_g2s(smem0 + (uint32_t)(st + C::OPER - smem), a_lo + (size_t)kc * C::OPER, C::OPER, afull(s));
+    };
 
     for (int item = blockIdx.x; item < bt.n_items && ok; item += gridDim.x) {
         int sgi = 0;
@@ -252,42 +397,40 @@ __global__ void __launch_bounds__(kTcThreads, 1) fused_tc_kernel(const __grid_co
 #pragma unroll
         for (int s = 0; s < kSub; ++s) acc[s] = make_float2(0.f, 0.f);
 
+        RawB<TERMS> raw;
+        load_b<TERMS>(sg, (long long)F * kFrame, 0, tid, raw);
+        if (tid == 0) issue_a(a_hi, a_lo, 0, 0);         // both stages are free at a pass start
         for (int ps = 0; ps < kTds * kPol && ok; ++ps) {
             const int blk = ps >> 1, pol = ps & 1;
             const uint32_t sel = 0x4400u | ((2u + pol) << 4) | (uint32_t)pol;
-            const long long row0 = (long long)F * kFrame + blk * kUp;
             for (int kc = 0; kc < C::NCH; ++kc) {
                 const int s = kc & 1;
                 if (kc >= 2) {
-                    if (!mbar_wait(s ? mbar1 : mbar0, s ? ph1 : ph0)) ok = false;
-                    if (s) ph1 ^= 1; else ph0 ^= 1;
+                    if (!mbar_wait(empty(s), par(pe, s))) ok = false;
+                    pe ^= 1u << s;
                 }
                 unsigned char* st = stage_base + s * C::STAGE;
-                unsigned char* sa_hi = st;
-                unsigned char* sa_lo = st + C::OPER;
                 unsigned char* sb_hi = st + (C::A_LO ? 2 : 1) * C::OPER;
                 unsigned char* sb_lo = sb_hi + C::OPER;
-                produce_b<TERMS>(sg, row0, kc, sel, w, sb_hi, sb_lo, tid);
+                RawB<TERMS> cur = raw;
                 {
-                    const uint4* src = reinterpret_cast<const uint4*>(a_hi + (size_t)kc * C::OPER);
-                    uint4* dst = reinterpret_cast<uint4*>(sa_hi);
-                    for (int i = tid; i < C::OPER / 16; i += kTcThreads) dst[i] = __ldg(src + i);
-                    if constexpr (C::A_LO) {
-                        const uint4* src2 = reinterpret_cast<const uint4*>(a_lo + (size_t)kc * C::OPER);
-                        uint4* dst2 = reinterpret_cast<uint4*>(sa_lo);
-                        for (int i = tid; i < C::OPER / 16; i += kTcThreads) dst2[i] = __ldg(src2 + i);
+                    const bool last = kc + 1 == C::NCH;
+                    if (!last || ps + 1 < kTds * kPol) {
+                        const int nblk = last ? ((ps + 1) >> 1) : blk;
+                        load_b<TERMS>(sg, (long long)F * kFrame + nblk * kUp, last ? 0 : kc + 1, tid, raw);
                     }
                 }
+                build_b<TERMS>(cur, sel, w, sb_hi, sb_lo, tid);
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                if (!ok) abort_s = 1;
-                cta_sync();
-                if (abort_s) {
-                    ok = false;
-                    break;
-                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(bfull(s));
                 if (tid == 0) {
-                    const uint32_t ahi = smem0 + (uint32_t)(sa_hi - smem), alo = smem0 + (uint32_t)(sa_lo - smem);
-                    const uint32_t bhi = smem0 + (uint32_t)(sb_hi - smem), blo = smem0 + (uint32_t)(sb_lo - smem);
+                    if (!mbar_wait(bfull(s), par(pb, s)) || !mbar_wait(afull(s), par(pa, s))) ok = false;
+                    pb ^= 1u << s;
+                    pa ^= 1u << s;
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t ahi = smem0 + (uint32_t)(st - smem), alo = ahi + C::OPER;
+                    const uint32_t bhi = smem0 + (uint32_t)(sb_hi - smem), blo = bhi + C::OPER;
 #pragma unroll
                     for (int ks = 0; ks < C::KC / 16; ++ks) {
 #pragma unroll
@@ -303,54 +446,42 @@ __global__ void __launch_bounds__(kTcThreads, 1) fused_tc_kernel(const __grid_co
                                 mma_f16(d, smem_desc(alo + aoff, 128, C::SBO), db, 1u);
                         }
                     }
-                    mma_commit(s ? mbar1 : mbar0);
+                    mma_commit(empty(s));
+                    // start the next twiddle chunk once its stage is free (chunk kc - 1's MMAs done)
+                    const int nkc = kc + 1 < C::NCH ? kc + 1 : (ps + 1 < kTds * kPol ? 0 : -1);
+                    if (nkc >= 0) {
+                        const int ns = s ^ 1;
+                        if (kc >= 1 && !mbar_wait(empty(ns), par(pe, ns))) ok = false;   // no flip: all threads wait it below
+                        issue_a(a_hi, a_lo, nkc, ns);
+                    }
                 }
             }
-            if (!ok) break;
             // the last two commits cover every MMA of the pass
-            if (!mbar_wait(mbar0, ph0)) ok = false;
-            ph0 ^= 1;
-            if (!mbar_wait(mbar1, ph1)) ok = false;
-            ph1 ^= 1;
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            if (!mbar_wait(empty(0), par(pe, 0))) ok = false;
+            if (!mbar_wait(empty(1), par(pe, 1))) ok = false;
+            pe ^= 3u;
+            if (!ok) abort_s = 1;
+            cta_sync();                              // every thread takes the same exit decision
+            if (abort_s) ok = false;
             if (!ok) break;
 
             if constexpr (MODE == 2) {
-                // stage dump: X for bin m, times 0..127 of this block
                 float2* d = bt.dump + ((((long long)(F * kTds + blk) * kPol + pol) * kEw + j) * kNs + m) * kUp;
                 for (int c4 = 0; c4 < 4; ++c4) {
-                    cp y[16];
-                    tmem_ld64(tlane + hh * 256 + 64 * c4, y);
-#pragma unroll
-                    for (int b = 0; b < 16; ++b) {
-                        d[32 * c4 + b] = make_float2(y[b].re.x, y[b].im.x);
-                        d[32 * c4 + 16 + b] = make_float2(y[b].re.y, y[b].im.y);
-                    }
+                    float re[32], im[32];
+                    tmem_ld32f(tlane + 32 * c4, re);
+                    tmem_ld32f(tlane + 128 + 32 * c4, im);
+                    for (int b = 0; b < 32; ++b) d[32 * c4 + b] = make_float2(re[b], im[b]);
                 }
             } else {
-                // first up-channel pass, in place: 8-point DFT over a (t = 16 a + b) per residue pair
-#pragma unroll 1
-                for (int bp = 0; bp < 8; ++bp) {
-                    const int b0 = 2 * bp;
-                    cp z[8];
-                    tmem_ld8x4(tlane + hh * 256 + 2 * b0, z);
-                    dft8(z);
-#pragma unroll
-                    for (int c = 0; c < 8; ++c) {
-                        if (c) {
-                            const float4 tw = tw_s[bp * 8 + c];
-                            z[c] = cmulp(z[c], make_float2(tw.x, tw.y), make_float2(tw.z, tw.w));
-                        }
-                        tmem_st4(tlane + hh * 256 + 2 * (16 * c + b0), z[c].re.x, z[c].im.x, z[c].re.y, z[c].im.y);
-                    }
-                }
+                upchan_pass1_split(tlane, tw_s);
                 tmem_wait_st();
-                upchan_pass2(tlane, hh, acc,
-                             MODE == 1
-                                 ? bt.dump + ((((long long)(F * kTds + blk) * kPol + pol) * kEw + j) * kNs + m) * kUp
-                                 : nullptr);
+                upchan_pass2_split(tlane, acc,
+                                   MODE == 1 ? bt.dump + ((((long long)(F * kTds + blk) * kPol + pol) * kEw + j) * kNs + m) * kUp
+                                             : nullptr);
             }
-            // the next pass's MMAs are issued after a CTA barrier that orders them after these loads
+            // all TMEM reads of this pass finish before the next pass's first MMA
+            cta_sync();
         }
 
         if constexpr (MODE == 0) {
