@@ -37,21 +37,23 @@
 namespace chimebf {
 namespace {
 
-constexpr int kTcThreads = 256;
 constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s bound on every mbarrier wait
 
 template <int TERMS>
 struct TcCfg {
     static constexpr int KC = TERMS == 3 ? 32 : 64;              // K elements (FP16) per chunk
     static constexpr int NCH = 2 * kFeed / KC;                    // chunks per pass
-    static constexpr int NQUAD = KC / 8;                          // 4-feed quads per chunk
     static constexpr int SBO = KC / 8 * 128;                      // bytes between 8-row groups
     static constexpr int OPER = 256 * KC * 2;                     // bytes of one 256-row operand chunk
     static constexpr bool A_LO = TERMS == 3;
     static constexpr bool B_LO = TERMS >= 2;
-    static constexpr int STAGE = OPER * (1 + (A_LO ? 1 : 0) + 1 + (B_LO ? 1 : 0));
+    static constexpr int A_STAGE = OPER * (A_LO ? 2 : 1);         // twiddle ring stage
+    static constexpr int B_STAGE = OPER * (B_LO ? 2 : 1);         // data ring stage
+    static constexpr int NA = 3;                                  // twiddle ring depth
     static constexpr int NOCT = KC / 16;                          // 8-feed octets per chunk
-    static constexpr size_t SMEM = 2ull * STAGE + 8 * 8 * 16 + 64;   // + up-channel twiddles + 6 barriers
+    static constexpr int NT = 288;                                // 8 producer warps + 1 MMA warp
+    static constexpr int NPROD = 256;                             // producer threads
+    static constexpr size_t SMEM = (size_t)NA * A_STAGE + 2ull * B_STAGE + 8 * 8 * 16 + 8 * (6 + 2 * NA);
 };
 
 // Byte offset of element (row r, k) in a K-major operand chunk without
@@ -167,9 +169,9 @@ __device__ __forceinline__ void tmem_ld32f(uint32_t taddr, float (&v)[32]) {
 
 // First up-channel pass in place on the split layout (t = 16 a + b): 8-point
 // DFT over a for the residue pair (b0, b0 + 1), twiddled by exp(-2 pi i b c / 128).
-__device__ __forceinline__ void upchan_pass1_split(uint32_t base, const float4* tw_s) {
+__device__ __forceinline__ void upchan_pass1_split(uint32_t base, const float4* tw_s, int sub, int nsub) {
 #pragma unroll 1
-    for (int bp = 0; bp < 8; ++bp) {
+    for (int bp = sub; bp < 8; bp += nsub) {
         const int b0 = 2 * bp;
         cp z[8];
         tmem_ld_p1(base + b0, z);
@@ -187,9 +189,10 @@ __device__ __forceinline__ void upchan_pass1_split(uint32_t base, const float4* 
 }
 
 // Second pass on the split layout: Re of (c, b) at 16 c + b, Im at 128 + 16 c + b.
-__device__ __forceinline__ void upchan_pass2_split(uint32_t base, float2 (&acc)[kSub], float2* dump) {
+__device__ __forceinline__ void upchan_pass2_split(uint32_t base, float2 (&acc)[kSub], float2* dump, int sub,
+                                                   int nsub) {
 #pragma unroll 1
-    for (int cpi = 0; cpi < 4; ++cpi) {
+    for (int cpi = sub; cpi < 4; cpi += nsub) {
         float re[32], im[32];
         tmem_ld32f(base + 32 * cpi, re);
         tmem_ld32f(base + 128 + 32 * cpi, im);
@@ -224,7 +227,8 @@ __device__ __forceinline__ uint32_t h2u(__half2 h) { return *reinterpret_cast<ui
 // 128-byte line.
 template <int TERMS>
 struct RawB {
-    static constexpr int TASKS = kUp * TcCfg<TERMS>::NOCT / kTcThreads;   // 2 (KC 64) or 1 (KC 32)
+    static constexpr int TASKS = kUp * TcCfg<TERMS>::NOCT / TcCfg<TERMS>::NPROD;   // 2 (KC 64) or 1 (KC 32)
+    static_assert(TASKS >= 1, "fewer producer tasks than threads");
     uint4 v[TASKS][kCyl];
 };
 
@@ -232,7 +236,7 @@ template <int TERMS>
 __device__ __forceinline__ void task_of(int tid, int i, int& t, int& oct) {
     using C = TcCfg<TERMS>;
     oct = (tid >> 5) % C::NOCT;
-    t = (tid & 31) + 32 * ((tid >> 5) / C::NOCT) + i * (kTcThreads / C::NOCT);
+    t = (tid & 31) + 32 * ((tid >> 5) / C::NOCT) + i * (C::NPROD / C::NOCT);
 }
 
 template <int TERMS>
@@ -324,28 +328,38 @@ __device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
 
 // MODE: 0 = detect and integrate, 1 = dump up-channelised voltages,
 //       2 = dump the N-S/E-W beams of the GEMM (stage dump).
+//
+// Warps 0-7 produce B chunks and run the up-channel passes out of TMEM; warp 8
+// streams the twiddle chunks (bulk copies, NA-deep ring) and issues the MMAs.
+// Chunks are numbered globally per CTA (item, pass, kc) so every barrier
+// phase is consumed exactly once in order.
 template <int TERMS, int MODE>
-__global__ void __launch_bounds__(kTcThreads, 1) fused_tc_kernel(const __grid_constant__ Batch bt) {
+__global__ void __launch_bounds__(TcCfg<TERMS>::NT, 1) fused_tc_kernel(const __grid_constant__ Batch bt) {
     using C = TcCfg<TERMS>;
+    constexpr int NA = C::NA;
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ uint32_t tmem_base_s;
     __shared__ int abort_s;
-    unsigned char* stage_base = smem;
-    float4* tw_s = reinterpret_cast<float4*>(smem + 2 * C::STAGE);
-    uint64_t* mbar_s = reinterpret_cast<uint64_t*>(smem + 2 * C::STAGE + 8 * 8 * 16);
+    unsigned char* a_ring = smem;                                  // NA x A_STAGE
+    unsigned char* b_ring = smem + NA * C::A_STAGE;                // 2 x B_STAGE
+    float4* tw_s = reinterpret_cast<float4*>(b_ring + 2 * C::B_STAGE);
+    uint64_t* mbar_s = reinterpret_cast<uint64_t*>(reinterpret_cast<unsigned char*>(tw_s) + 8 * 8 * 16);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int ell = 32 * (warp & 3) + lane;
-    const int hh = warp >> 2;
+    const bool producer = warp < 8;
+    const int ell = 32 * (warp & 3) + lane;           // TMEM lane (quarter = warp & 3)
+    const int hh = (warp >> 2) & 1;                    // bin half: m = ell + 128 hh
     const int m = ell + 128 * hh;
     const uint32_t smem0 = static_cast<uint32_t>(__cvta_generic_to_shared(smem));
     const uint32_t bar0 = static_cast<uint32_t>(__cvta_generic_to_shared(&mbar_s[0]));
-    auto bar = [&](int i) { return bar0 + 8u * (uint32_t)i; };
-    // barrier i of stage s: empty (0 + s): the stage's MMAs are done; afull (2 + s):
-    // its twiddle chunk landed; bfull (4 + s): all 8 warps stored their part of B
-    auto empty = [&](int s) { return bar0 + 8u * (uint32_t)s; };
-    auto afull = [&](int s) { return bar0 + 8u * (uint32_t)(2 + s); };
-    auto bfull = [&](int s) { return bar0 + 8u * (uint32_t)(4 + s); };
+    // barriers: bfull[2] (8 producer warps), bempty[2] (MMA commit), afull[NA] (bulk copy),
+    //           aempty[NA] (MMA commit), accfull (pass's last commit), tfree (8 producer warps)
+    auto bfull = [&](int s) { return bar0 + 8u * (uint32_t)s; };
+    auto bempty = [&](int s) { return bar0 + 8u * (uint32_t)(2 + s); };
+    auto afull = [&](int a) { return bar0 + 8u * (uint32_t)(4 + a); };
+    auto aempty = [&](int a) { return bar0 + 8u * (uint32_t)(4 + NA + a); };
+    const uint32_t accfull = bar0 + 8u * (uint32_t)(4 + 2 * NA);
+    const uint32_t tfree = accfull + 8u;
 
     if (warp == 0) {
         const uint32_t dst = static_cast<uint32_t>(__cvta_generic_to_shared(&tmem_base_s));
@@ -353,13 +367,20 @@ __global__ void __launch_bounds__(kTcThreads, 1) fused_tc_kernel(const __grid_co
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 0) {
-        for (int i = 0; i < 4; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(bar(i)) : "memory");
-        for (int i = 4; i < 6; ++i)
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(bar(i)), "r"(kTcThreads / 32) : "memory");
+        for (int i = 0; i < 2; ++i) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 8;" :: "r"(bfull(i)) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(bempty(i)) : "memory");
+        }
+        for (int i = 0; i < NA; ++i) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(afull(i)) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(aempty(i)) : "memory");
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(accfull) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 8;" :: "r"(tfree) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         abort_s = 0;
     }
-    for (int i = tid; i < 64; i += kTcThreads) {
+    for (int i = tid; i < 64; i += C::NT) {
         const int it = i >> 3, c = i & 7;
         const float2 w0 = bt.tw128[(2 * it * c) & (kUp - 1)];
         const float2 w1 = bt.tw128[((2 * it + 1) * c) & (kUp - 1)];
@@ -367,134 +388,163 @@ __global__ void __launch_bounds__(kTcThreads, 1) fused_tc_kernel(const __grid_co
     }
     cta_sync();
     const uint32_t tmem = tmem_base_s;
-    const uint32_t tlane = tmem + (static_cast<uint32_t>(32 * (warp & 3)) << 16) + hh * 256;
-    // phase parities, one bit per stage (pa, pb: thread 0 only)
-    uint32_t pe = 0, pa = 0, pb = 0;
-    auto par = [](uint32_t bits, int s) { return (bits >> s) & 1u; };
-    bool ok = true;
+    constexpr int PASSES = kTds * kPol;
 
-    // Thread 0: bulk-copy twiddle chunk kc of table image `a` into stage s.
-    auto issue_a = [&](const unsigned char* a_hi, const unsigned char* a_lo, int kc, int s) {
-        unsigned char* st = stage_base + s * C::STAGE;
-        mbar_expect(afull(s), (C::A_LO ? 2 : 1) * C::OPER);
-        bulk_g2s(smem0 + (uint32_t)(st - smem), a_hi + (size_t)kc * C::OPER, C::OPER, afull(s));
-        if constexpr (C::A_LO)
-            bulk_g2s(smem0 + (uint32_t)(st + C::OPER - smem), a_lo + (size_t)kc * C::OPER, C::OPER, afull(s));
-    };
-
-    for (int item = blockIdx.x; item < bt.n_items && ok; item += gridDim.x) {
-        int sgi = 0;
-        while (sgi + 1 < bt.n_segs && bt.segs[sgi + 1].item_begin <= item) ++sgi;
-        const Seg& sg = bt.segs[sgi];
-        const int local = item - sg.item_begin;
-        const int F = local >> 2, j = local & 3;
-        EwW w;
-        load_ew(bt.ew, sg.table, j, w);
-        const unsigned char* a_hi = bt.a_tc + (size_t)sg.table * bt.a_tc_stride;
-        const unsigned char* a_lo = a_hi + (size_t)C::NCH * C::OPER;
-
-        float2 acc[kSub];
-#pragma unroll
-        for (int s = 0; s < kSub; ++s) acc[s] = make_float2(0.f, 0.f);
-
-        RawB<TERMS> raw;
-        load_b<TERMS>(sg, (long long)F * kFrame, 0, tid, raw);
-        if (tid == 0) issue_a(a_hi, a_lo, 0, 0);         // both stages are free at a pass start
-        for (int ps = 0; ps < kTds * kPol && ok; ++ps) {
-            const int blk = ps >> 1, pol = ps & 1;
-            const uint32_t sel = 0x4400u | ((2u + pol) << 4) | (uint32_t)pol;
-            for (int kc = 0; kc < C::NCH; ++kc) {
-                const int s = kc & 1;
-                if (kc >= 2) {
-                    if (!mbar_wait(empty(s), par(pe, s))) ok = false;
-                    pe ^= 1u << s;
+    if (!producer) {
+        // ------------------------------ MMA / copy warp ------------------------------
+        if (lane == 0) {
+            uint32_t p_bfull = 0, p_afull = 0, p_aempty = 0, p_tfree = 0;
+            long long c = 0;                                  // global chunk number
+            long long c_copy = 0;                             // next twiddle chunk to copy
+            const long long n_my_items = bt.n_items > (int)blockIdx.x
+                                             ? (bt.n_items - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+            const long long total = n_my_items * PASSES * C::NCH;
+            auto table_of = [&](long long cc) {
+                const int it = (int)blockIdx.x + (int)(cc / (PASSES * C::NCH)) * (int)gridDim.x;
+                int sgi = 0;
+                while (sgi + 1 < bt.n_segs && bt.segs[sgi + 1].item_begin <= it) ++sgi;
+                return bt.segs[sgi].table;
+            };
+            auto issue_copy = [&](long long cc) {
+                const int a = (int)(cc % NA), kc = (int)(cc % C::NCH);
+                const unsigned char* a_hi = bt.a_tc + (size_t)table_of(cc) * bt.a_tc_stride;
+                unsigned char* st = a_ring + a * C::A_STAGE;
+                mbar_expect(afull(a), C::A_STAGE);
+                bulk_g2s(smem0 + (uint32_t)(st - smem), a_hi + (size_t)kc * C::OPER, C::OPER, afull(a));
+                if constexpr (C::A_LO)
+                    bulk_g2s(smem0 + (uint32_t)(st + C::OPER - smem), a_hi + (size_t)(C::NCH + kc) * C::OPER,
+                             C::OPER, afull(a));
+            };
+            bool ok = true;
+            // prologue: the first NA - 1 twiddle chunks
+            for (; c_copy < total && c_copy < NA - 1; ++c_copy) issue_copy(c_copy);
+            for (; c < total && ok; ++c) {
+                const int s = (int)(c & 1), a = (int)(c % NA), kc = (int)(c % C::NCH);
+                if (kc == 0 && c > 0) {
+                    // the previous pass's accumulator has been read by the producers
+                    if (!mbar_wait(tfree, p_tfree)) ok = false;
+                    p_tfree ^= 1u;
                 }
-                unsigned char* st = stage_base + s * C::STAGE;
-                unsigned char* sb_hi = st + (C::A_LO ? 2 : 1) * C::OPER;
-                unsigned char* sb_lo = sb_hi + C::OPER;
-                RawB<TERMS> cur = raw;
-                {
+                if (!mbar_wait(bfull(s), (p_bfull >> s) & 1u)) ok = false;
+                p_bfull ^= 1u << s;
+                if (!mbar_wait(afull(a), (p_afull >> a) & 1u)) ok = false;
+                p_afull ^= 1u << a;
+                if (!ok) break;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t ahi = smem0 + (uint32_t)(a_ring + a * C::A_STAGE - smem), alo = ahi + C::OPER;
+                const uint32_t bhi = smem0 + (uint32_t)(b_ring + s * C::B_STAGE - smem), blo = bhi + C::OPER;
+#pragma unroll
+                for (int ks = 0; ks < C::KC / 16; ++ks) {
+#pragma unroll
+                    for (int mt = 0; mt < 2; ++mt) {
+                        const uint32_t d = tmem + mt * 256;
+                        const uint32_t aoff = mt * 16 * C::SBO + ks * 256;
+                        const uint64_t da = smem_desc(ahi + aoff, 128, C::SBO);
+                        const uint64_t db = smem_desc(bhi + ks * 256, 128, C::SBO);
+                        mma_f16(d, da, db, (kc | ks) ? 1u : 0u);
+                        if constexpr (C::B_LO) mma_f16(d, da, smem_desc(blo + ks * 256, 128, C::SBO), 1u);
+                        if constexpr (C::A_LO) mma_f16(d, smem_desc(alo + aoff, 128, C::SBO), db, 1u);
+                    }
+                }
+                mma_commit(bempty(s));
+                mma_commit(aempty(a));
+                if (kc == C::NCH - 1) mma_commit(accfull);
+                // refill: chunk c + NA - 1 goes into the stage of chunk c - 1 once its MMAs are done
+                if (c_copy < total) {
+                    if (c_copy >= NA) {
+                        const int ra = (int)(c_copy % NA);
+                        if (!mbar_wait(aempty(ra), (p_aempty >> ra) & 1u)) ok = false;
+                        p_aempty ^= 1u << ra;
+                    }
+                    issue_copy(c_copy);
+                    ++c_copy;
+                }
+                if (abort_s) ok = false;
+            }
+            if (!ok) abort_s = 1;
+        }
+        __syncwarp();
+    } else {
+        // ------------------------------ producer warps ------------------------------
+        const uint32_t tlane = tmem + (static_cast<uint32_t>(32 * (warp & 3)) << 16) + hh * 256;
+        uint32_t p_bempty = 0, p_acc = 0;
+        long long c = 0;
+        bool ok = true;
+        for (int item = blockIdx.x; item < bt.n_items && ok; item += gridDim.x) {
+            int sgi = 0;
+            while (sgi + 1 < bt.n_segs && bt.segs[sgi + 1].item_begin <= item) ++sgi;
+            const Seg& sg = bt.segs[sgi];
+            const int local = item - sg.item_begin;
+            const int F = local >> 2, j = local & 3;
+            EwW w;
+            load_ew(bt.ew, sg.table, j, w);
+            float2 acc[kSub];
+#pragma unroll
+            for (int q = 0; q < kSub; ++q) acc[q] = make_float2(0.f, 0.f);
+            RawB<TERMS> raw;
+            load_b<TERMS>(sg, (long long)F * kFrame, 0, tid, raw);
+            for (int ps = 0; ps < PASSES && ok; ++ps) {
+                const int blk = ps >> 1, pol = ps & 1;
+                const uint32_t sel = 0x4400u | ((2u + pol) << 4) | (uint32_t)pol;
+                for (int kc = 0; kc < C::NCH && ok; ++kc, ++c) {
+                    const int s = (int)(c & 1);
+                    if (c >= 2) {
+                        if (!mbar_wait(bempty(s), (p_bempty >> s) & 1u)) ok = false;
+                        p_bempty ^= 1u << s;
+                    }
+                    unsigned char* sb_hi = b_ring + s * C::B_STAGE;
+                    unsigned char* sb_lo = sb_hi + C::OPER;
+                    RawB<TERMS> cur = raw;
                     const bool last = kc + 1 == C::NCH;
-                    if (!last || ps + 1 < kTds * kPol) {
+                    if (!last || ps + 1 < PASSES) {
                         const int nblk = last ? ((ps + 1) >> 1) : blk;
                         load_b<TERMS>(sg, (long long)F * kFrame + nblk * kUp, last ? 0 : kc + 1, tid, raw);
                     }
+                    build_b<TERMS>(cur, sel, w, sb_hi, sb_lo, tid);
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(bfull(s));
+                    if (abort_s) ok = false;
                 }
-                build_b<TERMS>(cur, sel, w, sb_hi, sb_lo, tid);
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                if (!ok) break;
+                if (!mbar_wait(accfull, p_acc)) ok = false;
+                p_acc ^= 1u;
+                if (!ok) break;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                if constexpr (MODE == 2) {
+                    float2* d = bt.dump + ((((long long)(F * kTds + blk) * kPol + pol) * kEw + j) * kNs + m) * kUp;
+                    for (int c4 = 0; c4 < 4; ++c4) {
+                        float re[32], im[32];
+                        tmem_ld32f(tlane + 32 * c4, re);
+                        tmem_ld32f(tlane + 128 + 32 * c4, im);
+                        for (int b = 0; b < 32; ++b) d[32 * c4 + b] = make_float2(re[b], im[b]);
+                    }
+                } else {
+                    upchan_pass1_split(tlane, tw_s, 0, 1);
+                    tmem_wait_st();
+                    upchan_pass2_split(tlane, acc,
+                                       MODE == 1 ? bt.dump + ((((long long)(F * kTds + blk) * kPol + pol) * kEw + j) * kNs + m) * kUp
+                                                 : nullptr,
+                                       0, 1);
+                }
+                // this warp's TMEM reads of the pass are done
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                 __syncwarp();
-                if (lane == 0) mbar_arrive(bfull(s));
-                if (tid == 0) {
-                    if (!mbar_wait(bfull(s), par(pb, s)) || !mbar_wait(afull(s), par(pa, s))) ok = false;
-                    pb ^= 1u << s;
-                    pa ^= 1u << s;
-                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    const uint32_t ahi = smem0 + (uint32_t)(st - smem), alo = ahi + C::OPER;
-                    const uint32_t bhi = smem0 + (uint32_t)(sb_hi - smem), blo = bhi + C::OPER;
+                if (lane == 0) mbar_arrive(tfree);
+            }
+            if constexpr (MODE == 0) {
+                if (ok) {
+                    float* o = sg.out + (long long)(kNs * j + m) * sg.beam_stride + F;
 #pragma unroll
-                    for (int ks = 0; ks < C::KC / 16; ++ks) {
-#pragma unroll
-                        for (int mt = 0; mt < 2; ++mt) {
-                            const uint32_t d = tmem + mt * 256;
-                            const uint32_t aoff = mt * 16 * C::SBO + ks * 256;
-                            const uint64_t da = smem_desc(ahi + aoff, 128, C::SBO);
-                            const uint64_t db = smem_desc(bhi + ks * 256, 128, C::SBO);
-                            mma_f16(d, da, db, (kc | ks) ? 1u : 0u);
-                            if constexpr (C::B_LO)
-                                mma_f16(d, da, smem_desc(blo + ks * 256, 128, C::SBO), 1u);
-                            if constexpr (C::A_LO)
-                                mma_f16(d, smem_desc(alo + aoff, 128, C::SBO), db, 1u);
-                        }
-                    }
-                    mma_commit(empty(s));
-                    // start the next twiddle chunk once its stage is free (chunk kc - 1's MMAs done)
-                    const int nkc = kc + 1 < C::NCH ? kc + 1 : (ps + 1 < kTds * kPol ? 0 : -1);
-                    if (nkc >= 0) {
-                        const int ns = s ^ 1;
-                        if (kc >= 1 && !mbar_wait(empty(ns), par(pe, ns))) ok = false;   // no flip: all threads wait it below
-                        issue_a(a_hi, a_lo, nkc, ns);
-                    }
+                    for (int q = 0; q < kSub; ++q) o[(long long)q * sg.sub_stride] = acc[q].x + acc[q].y;
                 }
             }
-            // the last two commits cover every MMA of the pass
-            if (!mbar_wait(empty(0), par(pe, 0))) ok = false;
-            if (!mbar_wait(empty(1), par(pe, 1))) ok = false;
-            pe ^= 3u;
-            if (!ok) abort_s = 1;
-            cta_sync();                              // every thread takes the same exit decision
-            if (abort_s) ok = false;
-            if (!ok) break;
-
-            if constexpr (MODE == 2) {
-                float2* d = bt.dump + ((((long long)(F * kTds + blk) * kPol + pol) * kEw + j) * kNs + m) * kUp;
-                for (int c4 = 0; c4 < 4; ++c4) {
-                    float re[32], im[32];
-                    tmem_ld32f(tlane + 32 * c4, re);
-                    tmem_ld32f(tlane + 128 + 32 * c4, im);
-                    for (int b = 0; b < 32; ++b) d[32 * c4 + b] = make_float2(re[b], im[b]);
-                }
-            } else {
-                upchan_pass1_split(tlane, tw_s);
-                tmem_wait_st();
-                upchan_pass2_split(tlane, acc,
-                                   MODE == 1 ? bt.dump + ((((long long)(F * kTds + blk) * kPol + pol) * kEw + j) * kNs + m) * kUp
-                                             : nullptr);
-            }
-            // all TMEM reads of this pass finish before the next pass's first MMA
-            cta_sync();
         }
-
-        if constexpr (MODE == 0) {
-            if (ok) {
-                float* o = sg.out + (long long)(kNs * j + m) * sg.beam_stride + F;
-#pragma unroll
-                for (int s = 0; s < kSub; ++s) o[(long long)s * sg.sub_stride] = acc[s].x + acc[s].y;
-            }
-        }
+        if (!ok) abort_s = 1;
     }
 
-    if (!ok && bt.status) atomicExch(bt.status, 1);
     cta_sync();
+    if (abort_s && tid == 0 && bt.status) atomicExch(bt.status, 1);
     if (warp == 0) {
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" :: "r"(tmem) : "memory");
     }
@@ -506,7 +556,7 @@ cudaError_t launch_tc(const Batch& b, int grid, cudaStream_t s) {
     const int smem = (int)TcCfg<TERMS>::SMEM;
     cudaError_t e = cudaFuncSetAttribute(fused_tc_kernel<TERMS, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    fused_tc_kernel<TERMS, MODE><<<grid, kTcThreads, smem, s>>>(b);
+    fused_tc_kernel<TERMS, MODE><<<grid, TcCfg<TERMS>::NT, smem, s>>>(b);
     return cudaGetLastError();
 }
 

@@ -6,7 +6,7 @@
 // mode a thread that batches queued requests of different streams into one
 // launch of the fused kernel (continuous batching: requests that arrive while
 // a batch runs join the next one, admitted against a memory budget).
-#include "../../include/chimebf.h"
+#include "chimebf.h"
 #include "bf_internal.h"
 
 #include <cuda_fp16.h>
