@@ -36,6 +36,34 @@ FLOP_PER_SAMPLE = 162.0          # conventional 5 N log2 N FFT count + E-W + det
 BYTES_PER_SAMPLE = 1.0 + 1024 * 16 * 4 / (384 * 2048)   # 1 B in + float32 out
 
 
+KERNEL_SOURCES = {
+    "fused_fp32_kernel": ["fused_fp32.cu", "device_common.cuh", "bf_internal.h"],
+    "fused_tc_kernel": ["fused_tc.cu", "device_common.cuh", "bf_internal.h"],
+}
+
+
+def kernel_hash(kernel: str) -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES[kernel]:
+        with open(os.path.join(ROOT, "paper_1702_04728_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def recorded_traffic(kernel: str, form: str):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel's
+    sources are unchanged since the capture (else None)."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            rec = json.load(f)[form]
+    except (OSError, KeyError, ValueError):
+        return None
+    if rec.get("source_sha256") != kernel_hash(kernel):
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -114,6 +142,36 @@ def make_input(rank: int, world: int = 1):
     freqs = D.rank_channels(rank, world)
     raw, _, _ = synth.config_node_slice(seed=D.rank_seed(rank), freqs=freqs)
     return raw, freqs
+
+
+def sweep_run(B, torch, stream, ws, steps=3):
+    """64 channels over 400-800 MHz x 390625 samples (1 s) x 2048 inputs = 51.2 GB,
+    counter-based noise generated on the device; device-timed per form."""
+    from paper_1702_04728_gb300 import synth
+    n_chan, T = 64, 390625
+    vin = synth.hash_noise_device(11, n_chan, T)
+    out = torch.empty(1024, 16 * n_chan, T // 384, dtype=torch.float32, device="cuda")
+    res = {"workload": "64 ch (400-800 MHz) x 390625 samples x 2048 inputs (51.2 GB), noise only",
+           "forms": []}
+    for fid, fname in [(B.BF_FP32_FFT, "fp32_fft"), (B.BF_TC_DFT256_X1, "tc_dft256_1term")]:
+        p = B.Plan(stream=stream, form=fid)
+        _, t = p.submit(vin, synth.SWEEP_FREQS, out, stream_id=3, flags=B.BF_END_OF_STREAM)
+        p.poll(t)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        tk = [p.submit(vin, synth.SWEEP_FREQS, out, stream_id=3, flags=B.BF_END_OF_STREAM)[1] for _ in range(steps)]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        for t in tk:
+            p.poll(t)
+        p.close()
+        ms = e0.elapsed_time(e1) / steps
+        res["forms"].append({"form": fname, "ms_per_step": ms,
+                             "input_samples_per_s": n_chan * T * N_INPUT / (ms * 1e-3)})
+    del vin, out
+    torch.cuda.empty_cache()
+    return res
 
 
 def serving_run(B, torch, capacity_sps, load, seconds, n_streams=200, seed=0, form=0):
@@ -235,6 +293,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=30)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serving-seconds", type=float, default=2.0)
+    ap.add_argument("--sweep", type=int, default=1, help="time the 64-channel x 1 s sweep (0: skip)")
     ap.add_argument("--form", default="BF_FP32_FFT",
                     choices=["BF_FP32_FFT", "BF_TC_DFT256", "BF_TC_DFT256_X2", "BF_TC_DFT256_X1"])
     args = ap.parse_args()
@@ -379,14 +438,15 @@ def main():
         if terms:
             achieved = 2048.0 * terms * samples / (ms * 1e-3) / 1e12
             roof = {"bound": "tensor", "achieved": achieved, "peak": peaks.get("bf16_tflops", 1927.5),
-                    "unit": "TFLOP/s", "frac": achieved / peaks.get("bf16_tflops", 1927.5), "traffic": None,
+                    "unit": "TFLOP/s", "frac": achieved / peaks.get("bf16_tflops", 1927.5),
+                    "traffic": recorded_traffic("fused_tc_kernel", fname),
                     "peak_note": f"dense FP16 tensor peak = measured bf16 burst ({peak_kind}; FP16 and BF16 "
                                  f"share the rate); achieved = 2048 x {terms} GEMM flop per input-sample"}
         else:
             alu_peak = n_sm * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
             achieved = FLOP_PER_SAMPLE * samples / (ms * 1e-3) / 1e12
             roof = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
-                    "frac": achieved / alu_peak, "traffic": None,
+                    "frac": achieved / alu_peak, "traffic": recorded_traffic("fused_fp32_kernel", fname),
                     "peak_note": f"FP32 FMA pipe: {n_sm} SMs x 128 lanes x 2 flop x "
                                  f"{peaks.get('sm_max_mhz', 2070.0):.0f} MHz ({peak_kind} max clock); "
                                  f"achieved = {FLOP_PER_SAMPLE:.0f} algorithmic flop per input-sample"}
@@ -408,10 +468,15 @@ def main():
             "forms": form_runs,
             "clocks": clocks,
         }
+        if args.sweep:
+            line["sweep"] = sweep_run(B, torch, stream, ws)
         if args.serving_seconds > 0:
             cap = samples / (ms * 1e-3)
             line["serving"] = [serving_run(B, torch, cap, ld, args.serving_seconds, form=headline_form)
                                for ld in (0.5, 0.9)]
+            # the full-array offered load of 0.8 TB/s of packed voltage, above one GPU's capacity
+            line["serving"].append(serving_run(B, torch, cap, 0.8e12 / cap, min(1.0, args.serving_seconds),
+                                               form=headline_form))
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(raw, freqs, host_out.numpy(), form_outs)
         print(json.dumps(line), flush=True)

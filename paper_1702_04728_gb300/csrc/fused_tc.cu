@@ -399,11 +399,13 @@ __global__ void __launch_bounds__(TcCfg<TERMS>::NT, 1) fused_tc_kernel(const __g
             const long long n_my_items = bt.n_items > (int)blockIdx.x
                                              ? (bt.n_items - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
             const long long total = n_my_items * PASSES * C::NCH;
+            // table of the item that chunk cc belongs to; items only move forward, so
+            // the segment search resumes where the previous lookup stopped
+            int seg_cursor = 0;
             auto table_of = [&](long long cc) {
                 const int it = (int)blockIdx.x + (int)(cc / (PASSES * C::NCH)) * (int)gridDim.x;
-                int sgi = 0;
-                while (sgi + 1 < bt.n_segs && bt.segs[sgi + 1].item_begin <= it) ++sgi;
-                return bt.segs[sgi].table;
+                while (seg_cursor + 1 < bt.n_segs && bt.segs[seg_cursor + 1].item_begin <= it) ++seg_cursor;
+                return bt.segs[seg_cursor].table;
             };
             auto issue_copy = [&](long long cc) {
                 const int a = (int)(cc % NA), kc = (int)(cc % C::NCH);

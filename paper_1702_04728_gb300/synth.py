@@ -190,3 +190,86 @@ def quantized_noise_variance(sigma: float = 2.5, clip: int = 7) -> float:
             p = cdf(k + 0.5) - cdf(k - 0.5)
         var += p * k * k
     return var
+
+
+# --- counter-based noise for workloads too large to generate on the host -----------
+#
+# Byte i of a channel block is drawn from SplitMix64 (Steele, Lea and Flood,
+# 2014) of (seed, i): the two 32-bit halves of the 64-bit output pick the real
+# and imaginary parts through integer thresholds of the clipped, rounded normal
+# distribution.  The device generator (torch) and the host generator (numpy)
+# implement the same definition in integer arithmetic, so they agree bit for
+# bit and the oracle can rebuild any sampled frame on the host.
+
+_SM_GAMMA = 0x9E3779B97F4A7C15
+_SM_M1 = 0xBF58476D1CE4E5B9
+_SM_M2 = 0x94D049BB133111EB
+
+
+def noise_thresholds(sigma: float = 2.5, clip: int = 7):
+    """uint32 thresholds t_k (k = -clip .. clip-1): value = -clip + #{t_k <= u}."""
+    from math import erf, sqrt
+    out = []
+    for k in range(-clip, clip):
+        cdf = 0.5 * (1.0 + erf((k + 0.5) / (sigma * sqrt(2.0))))
+        out.append(min(2**32 - 1, int(cdf * 2**32)))
+    return out
+
+
+def _mix_np(x: np.ndarray) -> np.ndarray:
+    with np.errstate(over="ignore"):
+        z = x + np.uint64(_SM_GAMMA)
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(_SM_M1)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(_SM_M2)
+        return z ^ (z >> np.uint64(31))
+
+
+def hash_noise_rows(seed: int, chan: int, n_samples_per_chan: int, t0: int, t1: int,
+                    sigma: float = 2.5) -> np.ndarray:
+    """Host copy of rows [t0, t1) of channel `chan`: uint8 [t1 - t0][2048]."""
+    thr = np.array(noise_thresholds(sigma), dtype=np.uint64)
+    base = (np.uint64(seed) << np.uint64(40)) + np.uint64(chan * n_samples_per_chan * N_INPUT)
+    idx = base + np.arange(t0 * N_INPUT, t1 * N_INPUT, dtype=np.uint64)
+    z = _mix_np(idx)
+    lo = z & np.uint64(0xFFFFFFFF)
+    hi = z >> np.uint64(32)
+    re = -7 + (hi[:, None] >= thr[None, :]).sum(axis=1).astype(np.int16)
+    im = -7 + (lo[:, None] >= thr[None, :]).sum(axis=1).astype(np.int16)
+    return encode(re, im).reshape(t1 - t0, N_INPUT)
+
+
+def hash_noise_device(seed: int, n_chan: int, n_samples: int, device="cuda", sigma: float = 2.5,
+                      chunk: int = 1 << 26):
+    """Device generation of uint8 [n_chan][n_samples][2048] (same bytes as above)."""
+    import torch
+    thr = noise_thresholds(sigma)
+    out = torch.empty(n_chan * n_samples * N_INPUT, dtype=torch.uint8, device=device)
+    total = out.numel()
+    base = seed << 40
+    mask32 = 0xFFFFFFFF
+
+    def as_i64(v):                                   # uint64 constant as a wrapped int64
+        return v - (1 << 64) if v >= (1 << 63) else v
+
+    def srl(z, k):                                   # logical right shift of int64 bit patterns
+        return (z >> k) & ((1 << (64 - k)) - 1)
+
+    for s in range(0, total, chunk):
+        n = min(chunk, total - s)
+        z = torch.arange(s, s + n, dtype=torch.int64, device=device) + (base + as_i64(_SM_GAMMA))
+        z = (z ^ srl(z, 30)) * as_i64(_SM_M1)
+        z = (z ^ srl(z, 27)) * as_i64(_SM_M2)
+        z = z ^ srl(z, 31)
+        hi = srl(z, 32)
+        lo = z & mask32
+        re = torch.zeros(n, dtype=torch.int16, device=device)
+        im = torch.zeros(n, dtype=torch.int16, device=device)
+        for t in thr:
+            re += (hi >= t).to(torch.int16)
+            im += (lo >= t).to(torch.int16)
+        out[s:s + n] = (((re + 1) << 4) | (im + 1)).to(torch.uint8)   # (v + 8) with v = count - 7
+        del z, hi, lo, re, im
+    return out.view(n_chan, n_samples, N_INPUT)
+
+
+SWEEP_FREQS = [400e6 + 6.25e6 * (i + 0.5) for i in range(64)]
