@@ -153,6 +153,29 @@ int bf_destroy(bf_plan_t p);
 /* Message for the calling thread's last error ("" if none). */
 const char* bf_last_error(void);
 
+/* ---- products of the intensity output (enqueued on the plan's stream) ---- */
+
+/*
+ * Frequency- and time-summed sky map (the map of Fig. 3, Sec. 3.3): for each of
+ * the 1024 beams, the sum over its n_sub sub-channels and n_frames frames of a
+ * bf_submit output float [1024][n_sub][n_frames] (device, d_out) into
+ * d_map float [1024] (device).  Enqueued after earlier work on the plan's
+ * stream; returns at once.  FP32 accumulation in a fixed order.
+ */
+int bf_skymap(bf_plan_t p, const float* d_out, int64_t n_sub, int64_t n_frames, float* d_map);
+
+/*
+ * 8-bit intensity (Table 1 lists 8-bit integer output; the paper gives no
+ * scaling rule).  For each of n_rows rows of n_frames floats (a bf_submit
+ * output viewed as [1024 * n_sub][n_frames]): mean and standard deviation over
+ * the row, code = clip(floor(64 + 16 (x - mean) / std + 1/2), 0, 255) (a constant
+ * row gives 64), evaluated in FP64 with sums frame by frame.  d_codes uint8
+ * [n_rows][n_frames] and optional d_stats double [n_rows][2] (mean, std), both
+ * device, caller-owned.  Enqueued on the plan's stream; returns at once.
+ */
+int bf_rescale_u8(bf_plan_t p, const float* d_out, int64_t n_rows, int64_t n_frames, uint8_t* d_codes,
+                  double* d_stats);
+
 /* ---- inspection entry points (used by the parity tests) ------------------ */
 
 /* Host-only: the clamp table (Eq. 1) [n_feed] and E-W weights [n_ew][n_cyl]

@@ -231,3 +231,43 @@ def beamform_sample(raw: np.ndarray, freqs_hz: Sequence[float], picks,
         P = (np.abs(Y) ** 2).sum(axis=(0, 1))                   # [q']
         res[i] = P.reshape(g.n_sub, g.f_ds).sum(axis=1)
     return res
+
+
+# --- after the fan-beam path (NEXT items) -----------------------------------------------
+
+def sky_map(O: np.ndarray) -> np.ndarray:
+    """Frequency- and time-summed response per beam (the map of Fig. 3):
+    O [beam, sub, frame] -> [beam]."""
+    return np.asarray(O, dtype=np.float64).sum(axis=(1, 2))
+
+
+def rescale_u8(O: np.ndarray):
+    """8-bit output (Table 1 lists 8-bit integer intensity; the scaling rule is
+    not given).  Reading: per (beam, sub-channel) row, the mean and standard
+    deviation over the row's frames, code = clip(floor(64 + 16 z + 1/2), 0, 255)
+    with z = (x - mean) / std, i.e. -4 sigma .. +11.9 sigma in 1/16 sigma steps;
+    a constant row gets code 64.  Evaluated in FP64 in a fixed order: sums run
+    frame by frame, each operation rounded once.
+    Returns (codes uint8 [rows, frames], stats float64 [rows, 2] = mean, std)."""
+    X = np.asarray(O, dtype=np.float32).reshape(-1, O.shape[-1]).astype(np.float64)
+    rows, nf = X.shape
+    codes = np.empty((rows, nf), np.uint8)
+    stats = np.empty((rows, 2))
+    for r in range(rows):
+        s = 0.0
+        for v in X[r]:
+            s = s + v
+        mean = s / nf
+        q = 0.0
+        for v in X[r]:
+            d = v - mean
+            q = q + d * d
+        std = np.sqrt(q / nf)
+        stats[r] = (mean, std)
+        if std > 0.0:
+            z = (X[r] - mean) / std
+            c = np.floor((64.0 + 16.0 * z) + 0.5)
+        else:
+            c = np.full(nf, 64.0)
+        codes[r] = np.clip(c, 0, 255).astype(np.uint8)
+    return codes.reshape(O.shape), stats.reshape(O.shape[:-1] + (2,))

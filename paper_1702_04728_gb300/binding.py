@@ -23,7 +23,7 @@ BF_END_OF_STREAM = 1
 N_BEAMS, N_SUB, FRAME, N_INPUT = 1024, 16, 384, 2048
 
 SYMBOLS = ["bf_config_default", "bf_plan", "bf_frames_out", "bf_submit", "bf_poll", "bf_destroy",
-           "bf_last_error", "bf_debug_tables", "bf_debug_gemm", "bf_debug_unpack", "bf_debug_beams",
+           "bf_last_error", "bf_skymap", "bf_rescale_u8", "bf_debug_tables", "bf_debug_gemm", "bf_debug_unpack", "bf_debug_beams",
            "bf_debug_upchan"]
 
 
@@ -76,6 +76,8 @@ def lib() -> ctypes.CDLL:
         L.bf_debug_beams.argtypes = [P, D, P, I64, P]
         L.bf_debug_upchan.argtypes = [P, D, P, I64, P]
         L.bf_debug_gemm.argtypes = [P, D, P, I64, P]
+        L.bf_skymap.argtypes = [P, P, I64, I64, P]
+        L.bf_rescale_u8.argtypes = [P, P, I64, I64, P, P]
         for name in SYMBOLS:
             getattr(L, name).restype = ctypes.c_char_p if name == "bf_last_error" else I
         _lib = L
@@ -197,6 +199,14 @@ def bf_debug_gemm(plan: int, freq_hz: float, d_vin, n_samples: int, d_out) -> No
     _check(lib().bf_debug_gemm(plan, float(freq_hz), _ptr(d_vin), n_samples, _ptr(d_out)))
 
 
+def bf_skymap(plan: int, d_out, n_sub: int, n_frames: int, d_map) -> None:
+    _check(lib().bf_skymap(plan, _ptr(d_out), n_sub, n_frames, _ptr(d_map)))
+
+
+def bf_rescale_u8(plan: int, d_out, n_rows: int, n_frames: int, d_codes, d_stats=None) -> None:
+    _check(lib().bf_rescale_u8(plan, _ptr(d_out), n_rows, n_frames, _ptr(d_codes), _ptr(d_stats)))
+
+
 # ---- convenience over torch device memory (allocation and marshalling only) ----
 
 class Plan:
@@ -232,6 +242,21 @@ class Plan:
         rc, got = self.poll(t)
         assert got == nf
         return out
+
+    def skymap(self, out):
+        """float32 [1024] sum over sub-channels and frames of a run() output."""
+        import torch
+        m = torch.empty(N_BEAMS, dtype=torch.float32, device=out.device)
+        bf_skymap(self.handle, out, out.shape[1], out.shape[2], m)
+        return m
+
+    def rescale_u8(self, out):
+        """(codes uint8 like out, stats float64 [1024, n_sub, 2]) of a run() output."""
+        import torch
+        codes = torch.empty(out.shape, dtype=torch.uint8, device=out.device)
+        stats = torch.empty(out.shape[0], out.shape[1], 2, dtype=torch.float64, device=out.device)
+        bf_rescale_u8(self.handle, out, out.shape[0] * out.shape[1], out.shape[2], codes, stats)
+        return codes, stats
 
     def close(self) -> None:
         if self.handle:

@@ -66,6 +66,9 @@ int fused_fp32_max_grid(int device);   // CTAs that fit at once (1 per SM)
 // 1 = dump up-channelised voltages, 2 = dump the N-S/E-W beams of the GEMM.
 cudaError_t fused_tc_launch(const Batch& b, int terms, int mode, int grid, cudaStream_t s);
 size_t tc_a_bytes(int terms);    // bytes of one table's twiddle image(s)
+cudaError_t skymap_launch(const float* in, int n_beams, long long per_beam, float* map, cudaStream_t s);
+cudaError_t rescale_u8_launch(const float* in, long long rows, long long nf, uint8_t* codes, double* stats,
+                              cudaStream_t s);
 int tc_chunk_k(int terms);       // K elements per shared-memory chunk
 
 }  // namespace chimebf

@@ -1,0 +1,95 @@
+// Kernels that run on the fan-beam output (arXiv 1702.04728, Sec. 3, Sec. 3.3,
+// Table 1): the frequency- and time-summed sky map of Fig. 3 and the 8-bit
+// rescaling of the intensity listed in Table 1.
+#include "bf_internal.h"
+
+#include <cstdint>
+
+namespace chimebf {
+namespace {
+
+constexpr int kMapThreads = 256;
+
+// One CTA per beam: sum of the beam's [n_sub][n_frames] block (contiguous),
+// fixed-order tree reduction in FP32.
+__global__ void __launch_bounds__(kMapThreads) skymap_kernel(const float* __restrict__ in, long long per_beam,
+                                                             float* __restrict__ map) {
+    __shared__ float red[kMapThreads / 32];
+    const float* p = in + (long long)blockIdx.x * per_beam;
+    float s = 0.f;
+    const long long n4 = per_beam / 4;
+    const bool al = ((reinterpret_cast<uintptr_t>(p) & 15) == 0);
+    if (al) {
+        const float4* p4 = reinterpret_cast<const float4*>(p);
+        for (long long i = threadIdx.x; i < n4; i += kMapThreads) {
+            const float4 v = __ldg(p4 + i);
+            s += (v.x + v.y) + (v.z + v.w);
+        }
+        for (long long i = 4 * n4 + threadIdx.x; i < per_beam; i += kMapThreads) s += __ldg(p + i);
+    } else {
+        for (long long i = threadIdx.x; i < per_beam; i += kMapThreads) s += __ldg(p + i);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        float t = threadIdx.x < kMapThreads / 32 ? red[threadIdx.x] : 0.f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (threadIdx.x == 0) map[blockIdx.x] = t;
+    }
+}
+
+// One thread per (beam, sub-channel) row: mean and standard deviation over the
+// row's frames, then code = clip(floor(64 + 16 (x - mean) / std + 1/2), 0, 255).
+// FP64 throughout, sums frame by frame, every operation rounded once (the
+// _rn intrinsics keep the compiler from fusing multiply and add), so the codes
+// follow a fixed evaluation order.
+__global__ void rescale_u8_kernel(const float* __restrict__ in, long long rows, long long nf,
+                                  uint8_t* __restrict__ codes, double* __restrict__ stats) {
+    const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= rows) return;
+    const float* x = in + r * nf;
+    double s = 0.0;
+    for (long long f = 0; f < nf; ++f) s = __dadd_rn(s, (double)x[f]);
+    const double mean = __ddiv_rn(s, (double)nf);
+    double q = 0.0;
+    for (long long f = 0; f < nf; ++f) {
+        const double d = __dsub_rn((double)x[f], mean);
+        q = __dadd_rn(q, __dmul_rn(d, d));
+    }
+    const double sd = __dsqrt_rn(__ddiv_rn(q, (double)nf));
+    if (stats) {
+        stats[2 * r] = mean;
+        stats[2 * r + 1] = sd;
+    }
+    uint8_t* c = codes + r * nf;
+    for (long long f = 0; f < nf; ++f) {
+        double v = 64.0;
+        if (sd > 0.0) {
+            const double z = __ddiv_rn(__dsub_rn((double)x[f], mean), sd);
+            v = floor(__dadd_rn(__dadd_rn(64.0, __dmul_rn(16.0, z)), 0.5));
+        }
+        v = v < 0.0 ? 0.0 : (v > 255.0 ? 255.0 : v);
+        c[f] = (uint8_t)v;
+    }
+}
+
+}  // namespace
+
+cudaError_t skymap_launch(const float* in, int n_beams, long long per_beam, float* map, cudaStream_t s) {
+    if (n_beams <= 0) return cudaSuccess;
+    skymap_kernel<<<n_beams, kMapThreads, 0, s>>>(in, per_beam, map);
+    return cudaGetLastError();
+}
+
+cudaError_t rescale_u8_launch(const float* in, long long rows, long long nf, uint8_t* codes, double* stats,
+                              cudaStream_t s) {
+    if (rows <= 0 || nf <= 0) return cudaSuccess;
+    const int t = 128;
+    rescale_u8_kernel<<<(unsigned)((rows + t - 1) / t), t, 0, s>>>(in, rows, nf, codes, stats);
+    return cudaGetLastError();
+}
+
+}  // namespace chimebf

@@ -712,6 +712,25 @@ int bf_destroy(bf_plan_t p) {
     return rc;
 }
 
+// ---- products of the intensity output -------------------------------------------------------
+
+int bf_skymap(bf_plan_t p, const float* d_out, int64_t n_sub, int64_t n_frames, float* d_map) {
+    if (!p || n_sub < 0 || n_frames < 0 || !d_map || (n_sub * n_frames > 0 && !d_out))
+        return fail(BF_EINVAL, "bad argument");
+    CK(cudaSetDevice(p->device));
+    CK(skymap_launch(d_out, kBeams, (long long)(n_sub * n_frames), d_map, p->stream));
+    return BF_OK;
+}
+
+int bf_rescale_u8(bf_plan_t p, const float* d_out, int64_t n_rows, int64_t n_frames, uint8_t* d_codes,
+                  double* d_stats) {
+    if (!p || n_rows < 0 || n_frames < 0 || (n_rows * n_frames > 0 && (!d_out || !d_codes)))
+        return fail(BF_EINVAL, "bad argument");
+    CK(cudaSetDevice(p->device));
+    CK(rescale_u8_launch(d_out, (long long)n_rows, (long long)n_frames, d_codes, d_stats, p->stream));
+    return BF_OK;
+}
+
 // ---- inspection entry points ------------------------------------------------------------
 
 int bf_debug_tables(const bf_config* cfg, double freq_hz, int32_t* lut_out, float* ew_out) {

@@ -359,3 +359,37 @@ def test_brute_force_tiny_geometry(freq):
     got = O.beamform_channel(raw, freq, ns, ew, g)
     assert got.shape == ref.shape
     assert np.allclose(got, ref, rtol=1e-10, atol=1e-9)
+
+
+# --- products of the output (NEXT items) -------------------------------------------------
+
+def test_rescale_u8_rule():
+    O = np.zeros((2, 3, 8), np.float32)
+    O[0, 0] = 5.0                                        # constant row -> 64
+    O[0, 1] = np.tile([0.0, 1.0], 4)                     # mean 0.5, std 0.5 -> z = -1, +1
+    O[0, 2] = [0, 0, 0, 0, 0, 0, 0, 1000]                # one outlier: z = +sqrt(7) ~ 2.65
+    O[1, 0] = [1000, 1000, 1000, 1000, 1000, 1000, 1000, 0]   # z = -sqrt(7) for the last
+    O[1, 1] = np.arange(8)
+    O[1, 2] = [0, 0, 0, 0, 0, 0, 0, 1e30]
+    codes, stats = O_rescale(O)
+    assert np.all(codes[0, 0] == 64) and stats[0, 0, 1] == 0.0
+    assert np.array_equal(codes[0, 1], np.tile([48, 80], 4))
+    assert codes[0, 2, 7] == int(np.floor(64 + 16 * np.sqrt(7) + 0.5)) and codes[0, 2, 0] == int(np.floor(64 - 16 / np.sqrt(7) + 0.5))
+    assert codes[1, 0, 7] == int(np.floor(64 - 16 * np.sqrt(7) + 0.5))
+    assert np.allclose(stats[1, 1], [3.5, np.std(np.arange(8))])       # population std
+    z = (np.arange(8) - 3.5) / np.std(np.arange(8))
+    assert np.array_equal(codes[1, 1], np.clip(np.floor(64 + 16 * z + 0.5), 0, 255).astype(np.uint8))
+    assert codes[1, 2].max() <= 255 and codes[1, 2].min() >= 0
+
+
+def O_rescale(O):
+    return O_mod.rescale_u8(O)
+
+
+O_mod = O
+
+
+def test_sky_map_sums_subchannels_and_frames():
+    rng_ = np.random.default_rng(3)
+    X = rng_.random((1024, 32, 5))
+    assert np.allclose(O.sky_map(X), X.sum(axis=(1, 2)))
