@@ -356,6 +356,34 @@ def main():
         ms = ev0.elapsed_time(ev1) / args.steps
     clocks = clk.summary()
 
+    # products of the output (sky map, 8-bit rescale, dedispersion), device-timed
+    def timed(fn, reps=20):
+        fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    smap = torch.empty(1024, dtype=torch.float32, device="cuda")
+    codes = torch.empty(out.shape, dtype=torch.uint8, device="cuda")
+    stats_u8 = torch.empty(out.shape[0], out.shape[1], 2, dtype=torch.float64, device="cuda")
+    series = torch.empty(1024, out.shape[2], dtype=torch.float32, device="cuda")
+    out_bytes = out.numel() * 4
+    post = {"input": "node-slice output float32 [1024][64][128] (33.5 MB)"}
+    t_map = timed(lambda: B.bf_skymap(plan.handle, out, out.shape[1], out.shape[2], smap))
+    t_u8 = timed(lambda: B.bf_rescale_u8(plan.handle, out, out.shape[0] * out.shape[1], out.shape[2], codes,
+                                          stats_u8))
+    n_dd = B.bf_dedisperse(plan.handle, out, freqs, out.shape[2], 1.0, series)
+    t_dd = timed(lambda: B.bf_dedisperse(plan.handle, out, freqs, out.shape[2], 1.0, series))
+    post["skymap"] = {"ms": t_map, "GBps": out_bytes / (t_map * 1e-3) / 1e9}
+    post["rescale_u8"] = {"ms": t_u8, "GBps": (out_bytes + out.numel() * 1.25) / (t_u8 * 1e-3) / 1e9,
+                          "note": "FP64 statistics, three passes over each row"}
+    post["dedisperse_dm1"] = {"ms": t_dd, "frames_out": n_dd,
+                              "GBps": (1024 * 64 * n_dd * 4 + 1024 * n_dd * 4) / (t_dd * 1e-3) / 1e9}
+
     # every form on the same resident input (device-timed, same stream)
     form_runs = []
     form_outs = {}
@@ -466,6 +494,7 @@ def main():
                                                   "overlapping beamforming of channel c, D2H of each output"},
             "gpu_launches": args.steps,
             "forms": form_runs,
+            "post": post,
             "clocks": clocks,
         }
         if args.sweep:

@@ -165,6 +165,21 @@ const char* bf_last_error(void);
 int bf_skymap(bf_plan_t p, const float* d_out, int64_t n_sub, int64_t n_frames, float* d_map);
 
 /*
+ * Incoherent dedispersion to one nominal DM (the fourth kernel proposed in
+ * Sec. 3.2).  d_out is a bf_submit output float [1024][16*n_chan][n_frames] of
+ * channels chan_freq_hz (host [n_chan]).  Sub-channel s of channel c sits at
+ * f_c + (8 s + 3.5 - 64) * 390625/128 Hz; its delay in frames relative to the
+ * highest sub-channel is floor(((4.148808e3 * dm) * (1/(f f) - 1/(fmax fmax)))
+ * / 0.98304e-3 + 1/2) with f in MHz (FP64, that order).  Writes
+ * d_series float [1024][n_out] with n_out = n_frames - max delay (0 if
+ * negative; *n_out reports it): series[b][t] = sum_s out[b][s][t + d_s].
+ * The delay table goes to plan-owned device memory; the kernel is enqueued
+ * on the plan's stream and the call returns at once.
+ */
+int bf_dedisperse(bf_plan_t p, const float* d_out, int n_chan, const double* chan_freq_hz, int64_t n_frames,
+                  double dm, float* d_series, int64_t* n_out);
+
+/*
  * 8-bit intensity (Table 1 lists 8-bit integer output; the paper gives no
  * scaling rule).  For each of n_rows rows of n_frames floats (a bf_submit
  * output viewed as [1024 * n_sub][n_frames]): mean and standard deviation over

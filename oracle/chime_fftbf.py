@@ -271,3 +271,45 @@ def rescale_u8(O: np.ndarray):
             c = np.full(nf, 64.0)
         codes[r] = np.clip(c, 0, 255).astype(np.uint8)
     return codes.reshape(O.shape), stats.reshape(O.shape[:-1] + (2,))
+
+
+K_DM_S_MHZ2 = 4.148808e3        # dispersion constant, s MHz^2 / (pc cm^-3)
+
+
+def subchannel_freqs(freqs_hz, g: Geometry = CHIME, chan_bw_hz: float = 390625.0) -> np.ndarray:
+    """Centre frequency of every output sub-channel [16 n_chan]: fine channel q'
+    sits at f + (q' - U/2) * bw/U (q' = 0 lowest), a sub-channel averages its
+    f_ds fine channels."""
+    fine = chan_bw_hz / g.upchan
+    out = []
+    for f in freqs_hz:
+        for s in range(g.n_sub):
+            out.append(float(f) + (g.f_ds * s + (g.f_ds - 1) / 2.0 - g.upchan // 2) * fine)
+    return np.array(out)
+
+
+def dedisperse_delays(freqs_hz, dm: float, frame_s: float = 384 * 2.56e-6, g: Geometry = CHIME) -> np.ndarray:
+    """Delay in frames of every sub-channel relative to the highest one:
+    floor(((K_DM DM) (1/(f f) - 1/(f_max f_max))) / T_frame + 1/2), f in MHz,
+    FP64 in that order (Sec. 3.2: dispersion delays the lower frequencies)."""
+    fs = [float(f) / 1e6 for f in subchannel_freqs(freqs_hz, g)]
+    fmax = max(fs)
+    out = []
+    for f in fs:
+        x = ((K_DM_S_MHZ2 * float(dm)) * (1.0 / (f * f) - 1.0 / (fmax * fmax))) / frame_s
+        out.append(int(np.floor(x + 0.5)))
+    return np.array(out)
+
+
+def dedisperse(O: np.ndarray, freqs_hz, dm: float, g: Geometry = CHIME):
+    """Incoherent dedispersion of the intensity output to one nominal DM (the
+    fourth kernel proposed in Sec. 3.2): series[beam, t] = sum over sub-channels
+    s of O[beam, s, t + d_s], for t < n_frames - max(d)."""
+    d = dedisperse_delays(freqs_hz, dm, g=g)
+    nf = O.shape[2]
+    n_out = max(0, nf - int(d.max()))
+    X = np.asarray(O, dtype=np.float64)
+    series = np.zeros((O.shape[0], n_out))
+    for s in range(O.shape[1]):
+        series += X[:, s, d[s]:d[s] + n_out]
+    return series, d

@@ -23,7 +23,7 @@ BF_END_OF_STREAM = 1
 N_BEAMS, N_SUB, FRAME, N_INPUT = 1024, 16, 384, 2048
 
 SYMBOLS = ["bf_config_default", "bf_plan", "bf_frames_out", "bf_submit", "bf_poll", "bf_destroy",
-           "bf_last_error", "bf_skymap", "bf_rescale_u8", "bf_debug_tables", "bf_debug_gemm", "bf_debug_unpack", "bf_debug_beams",
+           "bf_last_error", "bf_skymap", "bf_rescale_u8", "bf_dedisperse", "bf_debug_tables", "bf_debug_gemm", "bf_debug_unpack", "bf_debug_beams",
            "bf_debug_upchan"]
 
 
@@ -78,6 +78,7 @@ def lib() -> ctypes.CDLL:
         L.bf_debug_gemm.argtypes = [P, D, P, I64, P]
         L.bf_skymap.argtypes = [P, P, I64, I64, P]
         L.bf_rescale_u8.argtypes = [P, P, I64, I64, P, P]
+        L.bf_dedisperse.argtypes = [P, P, I, ctypes.POINTER(D), I64, D, P, ctypes.POINTER(I64)]
         for name in SYMBOLS:
             getattr(L, name).restype = ctypes.c_char_p if name == "bf_last_error" else I
         _lib = L
@@ -203,6 +204,16 @@ def bf_skymap(plan: int, d_out, n_sub: int, n_frames: int, d_map) -> None:
     _check(lib().bf_skymap(plan, _ptr(d_out), n_sub, n_frames, _ptr(d_map)))
 
 
+def bf_dedisperse(plan: int, d_out, freqs, n_frames: int, dm: float, d_series) -> int:
+    """Returns n_out (frames of the dedispersed series)."""
+    fptr, farr = _dbl_array(list(freqs))
+    n = ctypes.c_int64()
+    _check(lib().bf_dedisperse(plan, _ptr(d_out), len(freqs), fptr, n_frames, float(dm), _ptr(d_series),
+                               ctypes.byref(n)))
+    del farr
+    return n.value
+
+
 def bf_rescale_u8(plan: int, d_out, n_rows: int, n_frames: int, d_codes, d_stats=None) -> None:
     _check(lib().bf_rescale_u8(plan, _ptr(d_out), n_rows, n_frames, _ptr(d_codes), _ptr(d_stats)))
 
@@ -249,6 +260,14 @@ class Plan:
         m = torch.empty(N_BEAMS, dtype=torch.float32, device=out.device)
         bf_skymap(self.handle, out, out.shape[1], out.shape[2], m)
         return m
+
+    def dedisperse(self, out, freqs, dm: float):
+        """float32 [1024, n_out] series of a run() output dedispersed to `dm`."""
+        import torch
+        n_out = max(0, out.shape[2])           # upper bound; the library reports the exact length
+        series = torch.empty(N_BEAMS, n_out, dtype=torch.float32, device=out.device)
+        n = bf_dedisperse(self.handle, out, freqs, out.shape[2], dm, series)
+        return series[:, :n] if n else series[:, :0]
 
     def rescale_u8(self, out):
         """(codes uint8 like out, stats float64 [1024, n_sub, 2]) of a run() output."""

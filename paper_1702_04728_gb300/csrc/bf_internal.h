@@ -67,6 +67,8 @@ int fused_fp32_max_grid(int device);   // CTAs that fit at once (1 per SM)
 cudaError_t fused_tc_launch(const Batch& b, int terms, int mode, int grid, cudaStream_t s);
 size_t tc_a_bytes(int terms);    // bytes of one table's twiddle image(s)
 cudaError_t skymap_launch(const float* in, int n_beams, long long per_beam, float* map, cudaStream_t s);
+cudaError_t dedisperse_launch(const float* in, const int* delays, int n_sub, long long nf, long long n_out,
+                              float* out, cudaStream_t s);
 cudaError_t rescale_u8_launch(const float* in, long long rows, long long nf, uint8_t* codes, double* stats,
                               cudaStream_t s);
 int tc_chunk_k(int terms);       // K elements per shared-memory chunk

@@ -76,7 +76,29 @@ __global__ void rescale_u8_kernel(const float* __restrict__ in, long long rows, 
     }
 }
 
+// Incoherent dedispersion to one DM: series[beam][t] = sum over sub-channels s
+// (in order) of in[beam][s][t + d_s], t < n_out.  Threads run along t, so each
+// sub-channel row is read with coalesced loads.
+__global__ void dedisperse_kernel(const float* __restrict__ in, const int* __restrict__ delays, int n_sub,
+                                  long long nf, long long n_out, float* __restrict__ out) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int beam = blockIdx.y;
+    if (t >= n_out) return;
+    const float* row = in + (long long)beam * n_sub * nf + t;
+    float acc = 0.f;
+    for (int s = 0; s < n_sub; ++s) acc += __ldg(row + (long long)s * nf + delays[s]);
+    out[(long long)beam * n_out + t] = acc;
+}
+
 }  // namespace
+
+cudaError_t dedisperse_launch(const float* in, const int* delays, int n_sub, long long nf, long long n_out,
+                              float* out, cudaStream_t s) {
+    if (n_out <= 0) return cudaSuccess;
+    dim3 grid((unsigned)((n_out + 127) / 128), kBeams);
+    dedisperse_kernel<<<grid, 128, 0, s>>>(in, delays, n_sub, nf, n_out, out);
+    return cudaGetLastError();
+}
 
 cudaError_t skymap_launch(const float* in, int n_beams, long long per_beam, float* map, cudaStream_t s) {
     if (n_beams <= 0) return cudaSuccess;

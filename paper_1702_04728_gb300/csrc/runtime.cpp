@@ -105,6 +105,8 @@ struct bf_plan_s {
     int terms = 0;                            // tensor-core GEMM terms (0: FP32 FFT form)
     unsigned char* d_atc = nullptr;           // [kTcTableCap][tc_a_bytes(terms)] FP16 twiddle images
     int* h_status = nullptr;                  // mapped status word written by kernels
+    int* d_delays = nullptr;                  // dedispersion delay table (grown on demand)
+    size_t delays_cap = 0;
     int* d_status = nullptr;
 
     std::mutex mu;
@@ -706,6 +708,7 @@ int bf_destroy(bf_plan_t p) {
     cudaFree(p->d_tw512);
     cudaFree(p->d_tw128);
     if (p->d_atc) cudaFree(p->d_atc);
+    if (p->d_delays) cudaFree(p->d_delays);
     if (p->h_status) cudaFreeHost(p->h_status);
     if (p->own_stream) cudaStreamDestroy(p->stream);
     delete p;
@@ -719,6 +722,47 @@ int bf_skymap(bf_plan_t p, const float* d_out, int64_t n_sub, int64_t n_frames, 
         return fail(BF_EINVAL, "bad argument");
     CK(cudaSetDevice(p->device));
     CK(skymap_launch(d_out, kBeams, (long long)(n_sub * n_frames), d_map, p->stream));
+    return BF_OK;
+}
+
+int bf_dedisperse(bf_plan_t p, const float* d_out, int n_chan, const double* chan_freq_hz, int64_t n_frames,
+                  double dm, float* d_series, int64_t* n_out) {
+    if (!p || n_chan <= 0 || n_chan > 4096 || !chan_freq_hz || n_frames < 0 || !n_out || !(dm >= 0) ||
+        !std::isfinite(dm))
+        return fail(BF_EINVAL, "bad argument");
+    const int n_sub = kSub * n_chan;
+    const double fine = 390625.0 / kUp;
+    std::vector<double> fs(n_sub);
+    double fmax = 0.0;
+    for (int c = 0; c < n_chan; ++c) {
+        if (!(chan_freq_hz[c] > 0) || !std::isfinite(chan_freq_hz[c])) return fail(BF_EINVAL, "bad frequency");
+        for (int s = 0; s < kSub; ++s) {
+            const double f = (chan_freq_hz[c] + (kFds * s + (kFds - 1) / 2.0 - kUp / 2) * fine) / 1e6;
+            fs[c * kSub + s] = f;
+            fmax = std::max(fmax, f);
+        }
+    }
+    std::vector<int> d(n_sub);
+    int dmax = 0;
+    for (int i = 0; i < n_sub; ++i) {
+        const double x = ((4.148808e3 * dm) * (1.0 / (fs[i] * fs[i]) - 1.0 / (fmax * fmax))) / (kFrame * 2.56e-6);
+        d[i] = (int)std::floor(x + 0.5);
+        dmax = std::max(dmax, d[i]);
+    }
+    *n_out = std::max<int64_t>(0, n_frames - dmax);
+    if (*n_out == 0) return BF_OK;
+    if (!d_out || !d_series) return fail(BF_EINVAL, "null buffer");
+    CK(cudaSetDevice(p->device));
+    std::lock_guard<std::mutex> lk(p->mu);
+    if (p->delays_cap < (size_t)n_sub) {
+        if (p->d_delays) CK(cudaFree(p->d_delays));
+        p->d_delays = nullptr;
+        CK(cudaMalloc(&p->d_delays, (size_t)n_sub * sizeof(int)));
+        p->delays_cap = n_sub;
+    }
+    // pageable source: the copy is staged before the call returns, in stream order
+    CK(cudaMemcpyAsync(p->d_delays, d.data(), (size_t)n_sub * sizeof(int), cudaMemcpyHostToDevice, p->stream));
+    CK(dedisperse_launch(d_out, p->d_delays, n_sub, (long long)n_frames, (long long)*n_out, d_series, p->stream));
     return BF_OK;
 }
 

@@ -57,3 +57,28 @@ def test_rescale_u8_bit_exact():
     # z -> sqrt(39) = 6.24 (code ~164); noise frames stay below z = 6
     c = codes.cpu().numpy()
     assert c[:, :, 17].max() >= 64 + 16 * 6 and c[:, :, 16].max() < 64 + 16 * 6
+
+
+def test_dedisperse_matches_oracle_and_recovers_a_burst(built_lib):
+    freqs = [600e6 + 390625.0 * k for k in range(8)]
+    dm, T = 150.0, 384 * 64
+    m, j = 171, 3
+    s_src = (m - 127.5) / 128.0
+    u_src = math.sin(math.radians(0.6))
+    burst = synth.Burst(0.5, u=u_src, s=s_src, dm=dm, t0_s=0.4 * T * synth.DT_S, f_ref_hz=max(freqs))
+    raw = synth.make_voltages(freqs, T, seed=21, bursts=[burst])
+    with B.Plan() as p:
+        out = p.run(torch.from_numpy(raw).cuda(), freqs)
+        ser = p.dedisperse(out, freqs, dm).cpu().numpy()
+        ser0 = p.dedisperse(out, freqs, 0.0).cpu().numpy()
+        out_h = out.cpu().numpy()
+    ref, d = O.dedisperse(out_h, freqs, dm)
+    assert ser.shape == ref.shape and d.max() > 10
+    assert np.max(np.abs(ser - ref) / ref) <= 1e-5
+    beam = 256 * j + m
+
+    def snr(x):
+        return (x.max() - np.median(x)) / np.std(x)
+
+    assert snr(ser[beam]) > 1.5 * snr(ser0[beam][: ser.shape[1]])
+    assert int(np.argmax(ser.max(axis=1))) == beam
