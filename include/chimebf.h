@@ -183,7 +183,7 @@ int bf_dedisperse(bf_plan_t p, const float* d_out, int n_chan, const double* cha
  * 8-bit intensity (Table 1 lists 8-bit integer output; the paper gives no
  * scaling rule).  For each of n_rows rows of n_frames floats (a bf_submit
  * output viewed as [1024 * n_sub][n_frames]): mean and standard deviation over
- * the row, code = clip(floor(64 + 16 (x - mean) / std + 1/2), 0, 255) (a constant
+ * the row, code = clip(floor(64 + 16 (x - mean) (1/std) + 1/2), 0, 255) (a constant
  * row gives 64), evaluated in FP64 with sums frame by frame.  d_codes uint8
  * [n_rows][n_frames] and optional d_stats double [n_rows][2] (mean, std), both
  * device, caller-owned.  Enqueued on the plan's stream; returns at once.

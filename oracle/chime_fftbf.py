@@ -245,9 +245,9 @@ def rescale_u8(O: np.ndarray):
     """8-bit output (Table 1 lists 8-bit integer intensity; the scaling rule is
     not given).  Reading: per (beam, sub-channel) row, the mean and standard
     deviation over the row's frames, code = clip(floor(64 + 16 z + 1/2), 0, 255)
-    with z = (x - mean) / std, i.e. -4 sigma .. +11.9 sigma in 1/16 sigma steps;
-    a constant row gets code 64.  Evaluated in FP64 in a fixed order: sums run
-    frame by frame, each operation rounded once.
+    with z = (x - mean) * (1 / std), i.e. -4 sigma .. +11.9 sigma in 1/16 sigma
+    steps; a constant row gets code 64.  Evaluated in FP64 in a fixed order:
+    sums run frame by frame, each operation rounded once.
     Returns (codes uint8 [rows, frames], stats float64 [rows, 2] = mean, std)."""
     X = np.asarray(O, dtype=np.float32).reshape(-1, O.shape[-1]).astype(np.float64)
     rows, nf = X.shape
@@ -265,7 +265,8 @@ def rescale_u8(O: np.ndarray):
         std = np.sqrt(q / nf)
         stats[r] = (mean, std)
         if std > 0.0:
-            z = (X[r] - mean) / std
+            inv = 1.0 / std
+            z = (X[r] - mean) * inv
             c = np.floor((64.0 + 16.0 * z) + 0.5)
         else:
             c = np.full(nf, 64.0)

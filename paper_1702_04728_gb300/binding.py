@@ -264,10 +264,9 @@ class Plan:
     def dedisperse(self, out, freqs, dm: float):
         """float32 [1024, n_out] series of a run() output dedispersed to `dm`."""
         import torch
-        n_out = max(0, out.shape[2])           # upper bound; the library reports the exact length
-        series = torch.empty(N_BEAMS, n_out, dtype=torch.float32, device=out.device)
-        n = bf_dedisperse(self.handle, out, freqs, out.shape[2], dm, series)
-        return series[:, :n] if n else series[:, :0]
+        flat = torch.empty(N_BEAMS * max(1, out.shape[2]), dtype=torch.float32, device=out.device)
+        n = bf_dedisperse(self.handle, out, freqs, out.shape[2], dm, flat)
+        return flat[: N_BEAMS * n].view(N_BEAMS, n)
 
     def rescale_u8(self, out):
         """(codes uint8 like out, stats float64 [1024, n_sub, 2]) of a run() output."""

@@ -42,21 +42,37 @@ __global__ void __launch_bounds__(kMapThreads) skymap_kernel(const float* __rest
 }
 
 // One thread per (beam, sub-channel) row: mean and standard deviation over the
-// row's frames, then code = clip(floor(64 + 16 (x - mean) / std + 1/2), 0, 255).
-// FP64 throughout, sums frame by frame, every operation rounded once (the
+// row's frames, then code = clip(floor(64 + 16 (x - mean) (1 / std) + 1/2), 0,
+// 255).  FP64 throughout, sums frame by frame, every operation rounded once (the
 // _rn intrinsics keep the compiler from fusing multiply and add), so the codes
-// follow a fixed evaluation order.
-__global__ void rescale_u8_kernel(const float* __restrict__ in, long long rows, long long nf,
-                                  uint8_t* __restrict__ codes, double* __restrict__ stats) {
-    const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+// follow a fixed evaluation order.  A CTA stages its 32 rows through shared
+// memory with coalesced loads; rows longer than the stage are read directly.
+constexpr int kU8Rows = 32;
+constexpr int kU8Stage = 256;          // frames staged per row
+
+__global__ void __launch_bounds__(kU8Rows) rescale_u8_kernel(const float* __restrict__ in, long long rows,
+                                                               long long nf, uint8_t* __restrict__ codes,
+                                                               double* __restrict__ stats) {
+    __shared__ float st[kU8Rows][kU8Stage + 1];
+    const long long r0 = (long long)blockIdx.x * kU8Rows;
+    const long long r = r0 + threadIdx.x;
+    const bool staged = nf <= kU8Stage;
+    if (staged) {
+        // coalesced: the block's rows are contiguous in memory
+        const int nr = (int)min((long long)kU8Rows, rows - r0);
+        for (int rr = 0; rr < nr; ++rr)
+            for (long long f = threadIdx.x; f < nf; f += kU8Rows) st[rr][f] = __ldg(in + (r0 + rr) * nf + f);
+        __syncthreads();
+    }
     if (r >= rows) return;
     const float* x = in + r * nf;
+    auto val = [&](long long f) -> double { return staged ? (double)st[threadIdx.x][f] : (double)__ldg(x + f); };
     double s = 0.0;
-    for (long long f = 0; f < nf; ++f) s = __dadd_rn(s, (double)x[f]);
+    for (long long f = 0; f < nf; ++f) s = __dadd_rn(s, val(f));
     const double mean = __ddiv_rn(s, (double)nf);
     double q = 0.0;
     for (long long f = 0; f < nf; ++f) {
-        const double d = __dsub_rn((double)x[f], mean);
+        const double d = __dsub_rn(val(f), mean);
         q = __dadd_rn(q, __dmul_rn(d, d));
     }
     const double sd = __dsqrt_rn(__ddiv_rn(q, (double)nf));
@@ -64,11 +80,12 @@ __global__ void rescale_u8_kernel(const float* __restrict__ in, long long rows, 
         stats[2 * r] = mean;
         stats[2 * r + 1] = sd;
     }
+    const double inv = sd > 0.0 ? __ddiv_rn(1.0, sd) : 0.0;
     uint8_t* c = codes + r * nf;
     for (long long f = 0; f < nf; ++f) {
         double v = 64.0;
         if (sd > 0.0) {
-            const double z = __ddiv_rn(__dsub_rn((double)x[f], mean), sd);
+            const double z = __dmul_rn(__dsub_rn(val(f), mean), inv);
             v = floor(__dadd_rn(__dadd_rn(64.0, __dmul_rn(16.0, z)), 0.5));
         }
         v = v < 0.0 ? 0.0 : (v > 255.0 ? 255.0 : v);
@@ -109,8 +126,7 @@ cudaError_t skymap_launch(const float* in, int n_beams, long long per_beam, floa
 cudaError_t rescale_u8_launch(const float* in, long long rows, long long nf, uint8_t* codes, double* stats,
                               cudaStream_t s) {
     if (rows <= 0 || nf <= 0) return cudaSuccess;
-    const int t = 128;
-    rescale_u8_kernel<<<(unsigned)((rows + t - 1) / t), t, 0, s>>>(in, rows, nf, codes, stats);
+    rescale_u8_kernel<<<(unsigned)((rows + kU8Rows - 1) / kU8Rows), kU8Rows, 0, s>>>(in, rows, nf, codes, stats);
     return cudaGetLastError();
 }
 
