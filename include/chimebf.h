@@ -184,12 +184,13 @@ int bf_dedisperse(bf_plan_t p, const float* d_out, int n_chan, const double* cha
  * scaling rule).  For each of n_rows rows of n_frames floats (a bf_submit
  * output viewed as [1024 * n_sub][n_frames]): mean and standard deviation over
  * the row, code = clip(floor(64 + 16 (x - mean) (1/std) + 1/2), 0, 255) (a constant
- * row gives 64), evaluated in FP64 with sums frame by frame.  d_codes uint8
- * [n_rows][n_frames] and optional d_stats double [n_rows][2] (mean, std), both
+ * row gives 64), evaluated in FP32 with sums frame by frame, each operation
+ * rounded once.  d_codes uint8 [n_rows][n_frames] and optional d_stats float
+ * [n_rows][2] (mean, std), both
  * device, caller-owned.  Enqueued on the plan's stream; returns at once.
  */
 int bf_rescale_u8(bf_plan_t p, const float* d_out, int64_t n_rows, int64_t n_frames, uint8_t* d_codes,
-                  double* d_stats);
+                  float* d_stats);
 
 /* ---- inspection entry points (used by the parity tests) ------------------ */
 

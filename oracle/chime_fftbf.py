@@ -246,31 +246,30 @@ def rescale_u8(O: np.ndarray):
     not given).  Reading: per (beam, sub-channel) row, the mean and standard
     deviation over the row's frames, code = clip(floor(64 + 16 z + 1/2), 0, 255)
     with z = (x - mean) * (1 / std), i.e. -4 sigma .. +11.9 sigma in 1/16 sigma
-    steps; a constant row gets code 64.  Evaluated in FP64 in a fixed order:
-    sums run frame by frame, each operation rounded once.
-    Returns (codes uint8 [rows, frames], stats float64 [rows, 2] = mean, std)."""
-    X = np.asarray(O, dtype=np.float32).reshape(-1, O.shape[-1]).astype(np.float64)
+    steps; a constant row gets code 64.  Evaluated in FP32 (the precision of the
+    intensity) in a fixed order: sums run frame by frame, each operation
+    rounded once, so the integer codes are reproducible bit for bit.
+    Returns (codes uint8 like O, stats float32 [..., 2] = mean, std)."""
+    X = np.asarray(O, dtype=np.float32).reshape(-1, O.shape[-1])
     rows, nf = X.shape
-    codes = np.empty((rows, nf), np.uint8)
-    stats = np.empty((rows, 2))
-    for r in range(rows):
-        s = 0.0
-        for v in X[r]:
-            s = s + v
-        mean = s / nf
-        q = 0.0
-        for v in X[r]:
-            d = v - mean
-            q = q + d * d
-        std = np.sqrt(q / nf)
-        stats[r] = (mean, std)
-        if std > 0.0:
-            inv = 1.0 / std
-            z = (X[r] - mean) * inv
-            c = np.floor((64.0 + 16.0 * z) + 0.5)
-        else:
-            c = np.full(nf, 64.0)
-        codes[r] = np.clip(c, 0, 255).astype(np.uint8)
+    f32 = np.float32
+    s = np.zeros(rows, f32)
+    for f in range(nf):
+        s = s + X[:, f]
+    mean = s / f32(nf)
+    q = np.zeros(rows, f32)
+    for f in range(nf):
+        d = X[:, f] - mean
+        q = q + d * d
+    sd = np.sqrt(q / f32(nf))
+    pos = sd > 0
+    inv = np.zeros(rows, f32)
+    inv[pos] = f32(1.0) / sd[pos]
+    z = (X - mean[:, None]) * inv[:, None]
+    c = np.floor((f32(64.0) + f32(16.0) * z) + f32(0.5))
+    c[~pos] = 64.0
+    codes = np.clip(c, 0, 255).astype(np.uint8)
+    stats = np.stack([mean, sd], axis=1).astype(f32)
     return codes.reshape(O.shape), stats.reshape(O.shape[:-1] + (2,))
 
 

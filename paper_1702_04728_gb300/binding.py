@@ -272,7 +272,7 @@ class Plan:
         """(codes uint8 like out, stats float64 [1024, n_sub, 2]) of a run() output."""
         import torch
         codes = torch.empty(out.shape, dtype=torch.uint8, device=out.device)
-        stats = torch.empty(out.shape[0], out.shape[1], 2, dtype=torch.float64, device=out.device)
+        stats = torch.empty(out.shape[0], out.shape[1], 2, dtype=torch.float32, device=out.device)
         bf_rescale_u8(self.handle, out, out.shape[0] * out.shape[1], out.shape[2], codes, stats)
         return codes, stats
 

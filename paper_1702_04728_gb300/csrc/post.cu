@@ -43,8 +43,8 @@ __global__ void __launch_bounds__(kMapThreads) skymap_kernel(const float* __rest
 
 // One thread per (beam, sub-channel) row: mean and standard deviation over the
 // row's frames, then code = clip(floor(64 + 16 (x - mean) (1 / std) + 1/2), 0,
-// 255).  FP64 throughout, sums frame by frame, every operation rounded once (the
-// _rn intrinsics keep the compiler from fusing multiply and add), so the codes
+// 255).  FP32, sums frame by frame, every operation rounded once (the _rn
+// intrinsics keep the compiler from fusing multiply and add), so the codes
 // follow a fixed evaluation order.  A CTA stages its 32 rows through shared
 // memory with coalesced loads; rows longer than the stage are read directly.
 constexpr int kU8Rows = 32;
@@ -52,13 +52,12 @@ constexpr int kU8Stage = 256;          // frames staged per row
 
 __global__ void __launch_bounds__(kU8Rows) rescale_u8_kernel(const float* __restrict__ in, long long rows,
                                                                long long nf, uint8_t* __restrict__ codes,
-                                                               double* __restrict__ stats) {
+                                                               float* __restrict__ stats) {
     __shared__ float st[kU8Rows][kU8Stage + 1];
     const long long r0 = (long long)blockIdx.x * kU8Rows;
     const long long r = r0 + threadIdx.x;
     const bool staged = nf <= kU8Stage;
     if (staged) {
-        // coalesced: the block's rows are contiguous in memory
         const int nr = (int)min((long long)kU8Rows, rows - r0);
         for (int rr = 0; rr < nr; ++rr)
             for (long long f = threadIdx.x; f < nf; f += kU8Rows) st[rr][f] = __ldg(in + (r0 + rr) * nf + f);
@@ -66,29 +65,29 @@ __global__ void __launch_bounds__(kU8Rows) rescale_u8_kernel(const float* __rest
     }
     if (r >= rows) return;
     const float* x = in + r * nf;
-    auto val = [&](long long f) -> double { return staged ? (double)st[threadIdx.x][f] : (double)__ldg(x + f); };
-    double s = 0.0;
-    for (long long f = 0; f < nf; ++f) s = __dadd_rn(s, val(f));
-    const double mean = __ddiv_rn(s, (double)nf);
-    double q = 0.0;
+    auto val = [&](long long f) -> float { return staged ? st[threadIdx.x][f] : __ldg(x + f); };
+    float s = 0.f;
+    for (long long f = 0; f < nf; ++f) s = __fadd_rn(s, val(f));
+    const float mean = __fdiv_rn(s, (float)nf);
+    float q = 0.f;
     for (long long f = 0; f < nf; ++f) {
-        const double d = __dsub_rn(val(f), mean);
-        q = __dadd_rn(q, __dmul_rn(d, d));
+        const float d = __fsub_rn(val(f), mean);
+        q = __fadd_rn(q, __fmul_rn(d, d));
     }
-    const double sd = __dsqrt_rn(__ddiv_rn(q, (double)nf));
+    const float sd = __fsqrt_rn(__fdiv_rn(q, (float)nf));
     if (stats) {
         stats[2 * r] = mean;
         stats[2 * r + 1] = sd;
     }
-    const double inv = sd > 0.0 ? __ddiv_rn(1.0, sd) : 0.0;
+    const float inv = sd > 0.f ? __fdiv_rn(1.f, sd) : 0.f;
     uint8_t* c = codes + r * nf;
     for (long long f = 0; f < nf; ++f) {
-        double v = 64.0;
-        if (sd > 0.0) {
-            const double z = __dmul_rn(__dsub_rn(val(f), mean), inv);
-            v = floor(__dadd_rn(__dadd_rn(64.0, __dmul_rn(16.0, z)), 0.5));
+        float v = 64.f;
+        if (sd > 0.f) {
+            const float z = __fmul_rn(__fsub_rn(val(f), mean), inv);
+            v = floorf(__fadd_rn(__fadd_rn(64.f, __fmul_rn(16.f, z)), 0.5f));
         }
-        v = v < 0.0 ? 0.0 : (v > 255.0 ? 255.0 : v);
+        v = v < 0.f ? 0.f : (v > 255.f ? 255.f : v);
         c[f] = (uint8_t)v;
     }
 }
@@ -123,7 +122,7 @@ cudaError_t skymap_launch(const float* in, int n_beams, long long per_beam, floa
     return cudaGetLastError();
 }
 
-cudaError_t rescale_u8_launch(const float* in, long long rows, long long nf, uint8_t* codes, double* stats,
+cudaError_t rescale_u8_launch(const float* in, long long rows, long long nf, uint8_t* codes, float* stats,
                               cudaStream_t s) {
     if (rows <= 0 || nf <= 0) return cudaSuccess;
     rescale_u8_kernel<<<(unsigned)((rows + kU8Rows - 1) / kU8Rows), kU8Rows, 0, s>>>(in, rows, nf, codes, stats);

@@ -767,7 +767,7 @@ int bf_dedisperse(bf_plan_t p, const float* d_out, int n_chan, const double* cha
 }
 
 int bf_rescale_u8(bf_plan_t p, const float* d_out, int64_t n_rows, int64_t n_frames, uint8_t* d_codes,
-                  double* d_stats) {
+                  float* d_stats) {
     if (!p || n_rows < 0 || n_frames < 0 || (n_rows * n_frames > 0 && (!d_out || !d_codes)))
         return fail(BF_EINVAL, "bad argument");
     CK(cudaSetDevice(p->device));
