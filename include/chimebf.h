@@ -126,6 +126,10 @@ typedef struct {
     const uint8_t* vin;
     float* out;
     int flags;              /* 0 or BF_END_OF_STREAM */
+    const double* ew_sin_frames; /* tracking E-W beams (Sec. 3.1: "static or
+                               tracking"): host [n_frames_out][n_ew] sin of the
+                               E-W beam angles for each output frame of this
+                               request, or NULL for the plan's static beams */
 } bf_request;
 
 /* Frames a request will produce given the stream's current carry (host-side). */

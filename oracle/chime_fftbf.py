@@ -154,6 +154,23 @@ def ew_beams(X: np.ndarray, w: np.ndarray) -> np.ndarray:
     return np.einsum("tcpm,cj->tpjm", X, w)
 
 
+def ew_weights_tracking(freq_hz: float, ew_sin_frames: np.ndarray, g: Geometry = CHIME) -> np.ndarray:
+    """Tracking E-W beams (Sec. 3.1: the E-W beams may be static or track the
+    sky): beam j of output frame F points at ew_sin_frames[F, j].  Returns
+    w [F, c, j], each frame's weights defined as for static beams."""
+    u = np.asarray(ew_sin_frames, dtype=np.float64)
+    return np.stack([ew_weights(freq_hz, u[F], g) for F in range(u.shape[0])])
+
+
+def ew_beams_tracking(X: np.ndarray, W: np.ndarray, g: Geometry = CHIME) -> np.ndarray:
+    """X [T, c, p, m], W [F, c, j] -> B [F * frame, p, j, m]: sample t uses the
+    weights of the output frame t // frame it falls in; samples past the last
+    whole frame are dropped (they reach no output)."""
+    nf = W.shape[0]
+    Xf = X[:nf * g.frame].reshape(nf, g.frame, *X.shape[1:])
+    return np.einsum("ftcpm,fcj->ftpjm", Xf, W).reshape(nf * g.frame, X.shape[2], W.shape[2], X.shape[3])
+
+
 # --- a3: up-channelisation ------------------------------------------------------------
 
 def upchan_dft_matrix(g: Geometry = CHIME) -> np.ndarray:
@@ -188,11 +205,19 @@ def detect_downsample(Y: np.ndarray, g: Geometry = CHIME) -> np.ndarray:
 # --- whole path ---------------------------------------------------------------------------
 
 def beamform_channel(raw: np.ndarray, freq_hz: float, ns_sin=None, ew_sin=None,
-                     g: Geometry = CHIME, return_stages: bool = False):
-    """uint8 [T, 2048] of one coarse channel -> float64 [1024, 16, n_frames]."""
+                     g: Geometry = CHIME, return_stages: bool = False, ew_sin_frames=None):
+    """uint8 [T, 2048] of one coarse channel -> float64 [1024, 16, n_frames].
+
+    ew_sin_frames [n_frames, 4], if given, replaces the static E-W pointings
+    frame by frame (tracking beams)."""
     x = unpack(raw, g)
     X = ns_beams(x, clamp_lut(freq_hz, ns_sin, g), g)
-    B = ew_beams(X, ew_weights(freq_hz, ew_sin, g))
+    if ew_sin_frames is None:
+        B = ew_beams(X, ew_weights(freq_hz, ew_sin, g))
+    else:
+        if len(ew_sin_frames) != raw.shape[0] // g.frame:
+            raise ValueError("one row of E-W sines per output frame")
+        B = ew_beams_tracking(X, ew_weights_tracking(freq_hz, ew_sin_frames, g), g)
     Y = upchannelize(B, g)
     O = detect_downsample(Y, g)
     if return_stages:
@@ -201,9 +226,10 @@ def beamform_channel(raw: np.ndarray, freq_hz: float, ns_sin=None, ew_sin=None,
 
 
 def beamform(raw: np.ndarray, freqs_hz: Sequence[float], ns_sin=None, ew_sin=None,
-             g: Geometry = CHIME) -> np.ndarray:
+             g: Geometry = CHIME, ew_sin_frames=None) -> np.ndarray:
     """uint8 [n_chan, T, 2048] -> float64 [1024, 16 n_chan, n_frames]."""
-    outs = [beamform_channel(raw[c], f, ns_sin, ew_sin, g) for c, f in enumerate(freqs_hz)]
+    outs = [beamform_channel(raw[c], f, ns_sin, ew_sin, g, ew_sin_frames=ew_sin_frames)
+            for c, f in enumerate(freqs_hz)]
     return np.concatenate(outs, axis=1)
 
 

@@ -47,7 +47,8 @@ class bf_config(ctypes.Structure):
 class bf_request(ctypes.Structure):
     _fields_ = [("stream_id", ctypes.c_uint64), ("n_chan", ctypes.c_int),
                 ("chan_freq_hz", ctypes.POINTER(ctypes.c_double)), ("n_samples", ctypes.c_int64),
-                ("vin", ctypes.c_void_p), ("out", ctypes.c_void_p), ("flags", ctypes.c_int)]
+                ("vin", ctypes.c_void_p), ("out", ctypes.c_void_p), ("flags", ctypes.c_int),
+                ("ew_sin_frames", ctypes.POINTER(ctypes.c_double))]
 
 
 _lib = None
@@ -153,13 +154,18 @@ def bf_frames_out(plan: int, stream_id: int, n_samples: int) -> int:
 
 
 def bf_submit(plan: int, stream_id: int, freqs: Sequence[float], n_samples: int, vin, out,
-              flags: int = 0):
-    """Returns (status, ticket); status is BF_OK or BF_EQUEUED."""
+              flags: int = 0, ew_sin_frames=None):
+    """Returns (status, ticket); status is BF_OK or BF_EQUEUED.  ew_sin_frames:
+    optional [n_frames_out][4] E-W beam sines per output frame (tracking)."""
     fptr, farr = _dbl_array(list(freqs))
-    req = bf_request(stream_id, len(freqs), fptr, n_samples, _ptr(vin), _ptr(out), flags)
+    tptr, tarr = (None, None)
+    if ew_sin_frames is not None:
+        import numpy as np
+        tptr, tarr = _dbl_array(np.asarray(ew_sin_frames, dtype=np.float64).ravel().tolist())
+    req = bf_request(stream_id, len(freqs), fptr, n_samples, _ptr(vin), _ptr(out), flags, tptr)
     t = ctypes.c_uint64()
     rc = _check(lib().bf_submit(plan, ctypes.byref(req), ctypes.byref(t)))
-    del farr
+    del farr, tarr
     return rc, t.value
 
 
@@ -235,21 +241,22 @@ class Plan:
     def frames_out(self, stream_id: int, n_samples: int) -> int:
         return bf_frames_out(self.handle, stream_id, n_samples)
 
-    def submit(self, vin, freqs, out, stream_id: int = 0, flags: int = 0, n_samples: Optional[int] = None):
+    def submit(self, vin, freqs, out, stream_id: int = 0, flags: int = 0, n_samples: Optional[int] = None,
+               ew_sin_frames=None):
         if n_samples is None:
             n_samples = vin.shape[-2]
-        return bf_submit(self.handle, stream_id, freqs, n_samples, vin, out, flags)
+        return bf_submit(self.handle, stream_id, freqs, n_samples, vin, out, flags, ew_sin_frames)
 
     def poll(self, ticket: int, timeout_us: int = -1):
         return bf_poll(self.handle, ticket, timeout_us)
 
-    def run(self, vin, freqs, stream_id: int = 0, flags: int = BF_END_OF_STREAM):
+    def run(self, vin, freqs, stream_id: int = 0, flags: int = BF_END_OF_STREAM, ew_sin_frames=None):
         """vin: torch.uint8 CUDA tensor [n_chan, T, 2048] -> float32 [1024, 16 n_chan, n_frames]."""
         import torch
         n_chan, T = int(vin.shape[0]), int(vin.shape[1])
         nf = self.frames_out(stream_id, T)
         out = torch.empty((N_BEAMS, N_SUB * n_chan, nf), dtype=torch.float32, device=vin.device)
-        _, t = self.submit(vin, freqs, out, stream_id, flags, T)
+        _, t = self.submit(vin, freqs, out, stream_id, flags, T, ew_sin_frames)
         rc, got = self.poll(t)
         assert got == nf
         return out

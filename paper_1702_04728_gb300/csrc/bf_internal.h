@@ -38,6 +38,7 @@ struct Seg {
     int table;               // row of the per-frequency tables
     int item_begin;          // first work item; 4 items (E-W beams) per frame
     int pad_;
+    const float2* ew_frames; // tracking E-W beams: [n_frames][4 ew][4 cyl] phases, or null (static)
 };
 
 struct Batch {

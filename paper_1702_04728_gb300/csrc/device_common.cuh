@@ -169,6 +169,16 @@ __device__ __forceinline__ void load_ew(const float2* __restrict__ ew, int table
     }
 }
 
+// E-W weights of beam j for frame F of a segment: the per-frame table of a
+// tracking request, else the channel's static table.
+__device__ __forceinline__ void load_ew_frame(const Seg& sg, const float2* __restrict__ ew, int F, int j, EwW& w) {
+    if (sg.ew_frames) {
+        load_ew(sg.ew_frames, F, j, w);
+    } else {
+        load_ew(ew, sg.table, j, w);
+    }
+}
+
 __device__ __forceinline__ void load_row(const uint8_t* p, int lane, uint4 (&in)[kCyl]) {
 #pragma unroll
     for (int c = 0; c < kCyl; ++c)

@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(kThreads, 1) fused_fp32_kernel(const __grid_co
 
         for (int i = tid; i < kNs; i += kThreads) lut_s[i] = bt.lut[sg.table * kNs + i];
         EwW w;
-        load_ew(bt.ew, sg.table, j, w);
+        load_ew_frame(sg, bt.ew, F, j, w);
         cta_sync();
         const int Lsw = bsw(lut_s[m]);
 

@@ -479,7 +479,7 @@ __global__ void __launch_bounds__(TcCfg<TERMS>::NT, 1) fused_tc_kernel(const __g
             const int local = item - sg.item_begin;
             const int F = local >> 2, j = local & 3;
             EwW w;
-            load_ew(bt.ew, sg.table, j, w);
+            load_ew_frame(sg, bt.ew, F, j, w);
             float2 acc[kSub];
 #pragma unroll
             for (int q = 0; q < kSub; ++q) acc[q] = make_float2(0.f, 0.f);

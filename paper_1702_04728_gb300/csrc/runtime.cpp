@@ -77,6 +77,15 @@ struct Job {
     uint64_t ticket;
     bf_request req;
     std::vector<double> freqs;
+    int64_t track_frames = -1;      // >= 0: tracking E-W beams for this many output frames
+    std::vector<float2> track;      // [n_chan][track_frames][4 ew][4 cyl] phases (FP64-derived)
+};
+
+// Pinned staging + device copy of one batch's tracking tables.
+struct TrackBuf {
+    size_t bytes = 0;
+    float2* host = nullptr;
+    float2* dev = nullptr;
 };
 
 struct InflightBatch {
@@ -85,6 +94,7 @@ struct InflightBatch {
     std::vector<uint64_t> tickets;
     size_t bytes;
     std::vector<std::pair<size_t, uint8_t*>> release;   // carry buffers free once the batch is done
+    TrackBuf track;                                     // tracking tables, back to the pool at retire
 };
 
 }  // namespace
@@ -119,6 +129,7 @@ struct bf_plan_s {
     std::deque<InflightBatch> inflight;
     std::vector<cudaEvent_t> event_pool;
     std::multimap<size_t, uint8_t*> carry_pool;   // free carry buffers by size (reused, freed at destroy)
+    std::multimap<size_t, TrackBuf> track_pool;   // free tracking-table buffers by size
     size_t mem_in_use = 0;      // bytes of requests in launched, unretired batches
     size_t queued_bytes = 0;    // bytes of requests waiting in the queue
     bool stop = false;
@@ -158,14 +169,40 @@ void clamp_table(const bf_plan_s* p, double f, int32_t* lut) {
 
 // E-W phasing (Sec. 3): cylinder c at c * D, beam j toward u_j:
 // w[j][c] = exp(-2 pi i f c D u_j / c).
-void ew_table(const bf_plan_s* p, double f, float* ew) {
+// E-W phases of the four beams (Sec. 3: exact phasing across the cylinders):
+// w[j][c] = exp(-2 pi i frac(f c D u_j / c0)), products left to right in FP64.
+void ew_phases(const bf_plan_s* p, double f, const double* u, float* ew) {
     for (int j = 0; j < kEw; ++j)
         for (int c = 0; c < kCyl; ++c) {
-            const double cyc = (((f * c) * p->cfg.cyl_spacing_m) * p->ew_sin[j]) / kC0;
+            const double cyc = (((f * c) * p->cfg.cyl_spacing_m) * u[j]) / kC0;
             const double fr = cyc - std::floor(cyc);
             ew[2 * (j * kCyl + c)] = (float)std::cos(-2.0 * kPi * fr);
             ew[2 * (j * kCyl + c) + 1] = (float)std::sin(-2.0 * kPi * fr);
         }
+}
+
+void ew_table(const bf_plan_s* p, double f, float* ew) { ew_phases(p, f, p->ew_sin.data(), ew); }
+
+// Tracking buffer of at least `bytes` from the pool or new (pinned host + device).
+int track_alloc(bf_plan_s* p, size_t bytes, TrackBuf* out) {
+    auto it = p->track_pool.lower_bound(bytes);
+    if (it != p->track_pool.end()) {
+        *out = it->second;
+        p->track_pool.erase(it);
+        return BF_OK;
+    }
+    size_t cap = 4096;
+    while (cap < bytes) cap <<= 1;
+    TrackBuf t;
+    t.bytes = cap;
+    CK(cudaHostAlloc((void**)&t.host, cap, cudaHostAllocDefault));
+    cudaError_t e = cudaMalloc((void**)&t.dev, cap);
+    if (e != cudaSuccess) {
+        cudaFreeHost(t.host);
+        return cuda_fail(e, "cudaMalloc (tracking tables)");
+    }
+    *out = t;
+    return BF_OK;
 }
 
 // Tensor-core twiddle image of one frequency: A[m][2n] = cos, A[m][2n+1] = sin
@@ -324,12 +361,31 @@ int launch_jobs(bf_plan_s* p, std::vector<Job>& jobs, size_t bytes) {
     std::vector<Carry> carries;
     std::vector<Batch> batches;
     Batch b = make_batch(p);
+    // tracking tables of this launch: one pinned staging buffer, one copy
+    size_t track_elems = 0;
+    for (auto& jb : jobs) track_elems += jb.track.size();
+    TrackBuf tb;
+    if (track_elems) {
+        int rc = track_alloc(p, track_elems * sizeof(float2), &tb);
+        if (rc) return rc;
+    }
+    size_t track_off = 0;
     for (auto& jb : jobs) {
         StreamState* st = nullptr;
         int rc = stream_for(p, &jb.req, &st);
         if (rc) return rc;
         const int64_t nf = frames_for(p, &jb.req, st->carry_rows);
         const int new_rows = (int)((st->carry_rows + jb.req.n_samples) % kFrame);
+        if (jb.track_frames >= 0 && jb.track_frames != nf) {
+            if (tb.host) p->track_pool.emplace(tb.bytes, tb);
+            return fail(BF_EINVAL, "tracking table rows differ from the frames the request produces");
+        }
+        const float2* track_dev = nullptr;
+        if (!jb.track.empty()) {
+            std::memcpy(tb.host + track_off, jb.track.data(), jb.track.size() * sizeof(float2));
+            track_dev = tb.dev + track_off;
+            track_off += jb.track.size();
+        }
         p->tickets[jb.ticket].n_frames = nf;
         for (int c = 0; c < jb.req.n_chan && nf > 0; ++c) {
             if (b.n_segs == kMaxSegs) {
@@ -345,6 +401,7 @@ int launch_jobs(bf_plan_s* p, std::vector<Job>& jobs, size_t bytes) {
             s.carry_rows = st->carry_rows;
             s.n_frames = (int)nf;
             s.table = st->tables[c];
+            s.ew_frames = track_dev ? track_dev + (size_t)c * nf * kEw * kCyl : nullptr;
             s.item_begin = b.n_items;
             b.n_items += (int)nf * kEw;
         }
@@ -353,6 +410,14 @@ int launch_jobs(bf_plan_s* p, std::vector<Job>& jobs, size_t bytes) {
         st->carry_rows = new_rows;      // host view advances at launch time
     }
     if (b.n_segs) batches.push_back(b);
+    if (track_elems) {
+        cudaError_t e = cudaMemcpyAsync(tb.dev, tb.host, track_elems * sizeof(float2), cudaMemcpyHostToDevice,
+                                        p->stream);
+        if (e != cudaSuccess) {
+            p->track_pool.emplace(tb.bytes, tb);
+            return cuda_fail(e, "tracking table upload");
+        }
+    }
     for (auto& bb : batches) {
         bb.a_tc = p->d_atc;                       // tables may have been created above
         cudaError_t e = p->terms ? fused_tc_launch(bb, p->terms, 0, std::min(p->grid, bb.n_items), p->stream)
@@ -389,7 +454,7 @@ int launch_jobs(bf_plan_s* p, std::vector<Job>& jobs, size_t bytes) {
         CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
     }
     CK(cudaEventRecord(ev, p->stream));
-    InflightBatch ib{p->next_batch++, ev, {}, bytes, {}};
+    InflightBatch ib{p->next_batch++, ev, {}, bytes, {}, tb};
     for (auto& jb : jobs) {
         ib.tickets.push_back(jb.ticket);
         Ticket& t = p->tickets[jb.ticket];
@@ -432,6 +497,7 @@ bool retire(bf_plan_s* p) {
         }
         p->mem_in_use -= std::min(p->mem_in_use, ib.bytes);
         for (auto& r : ib.release) p->carry_pool.emplace(r.first, r.second);
+        if (ib.track.host) p->track_pool.emplace(ib.track.bytes, ib.track);
         p->event_pool.push_back(ib.ev);
         p->inflight.pop_front();
         any = true;
@@ -623,8 +689,25 @@ int bf_submit(bf_plan_t p, const bf_request* r, uint64_t* ticket) {
         if ((carry + r->n_samples) / kFrame > 0) return fail(BF_EINVAL, "null out with frames to write");
     }
     Job jb;
+    if (r->ew_sin_frames) {
+        // frames this request produces: the stream's carry advanced by its queued requests
+        int carry = sit != p->streams.end() ? sit->second.carry_rows : 0;
+        for (auto& q : p->queue)
+            if (q.req.stream_id == r->stream_id) carry = (int)((carry + q.req.n_samples) % kFrame);
+        const int64_t nf = (carry + r->n_samples) / kFrame;
+        for (int64_t i = 0; i < nf * kEw; ++i)
+            if (!std::isfinite(r->ew_sin_frames[i]) || std::fabs(r->ew_sin_frames[i]) > 1.0)
+                return fail(BF_EINVAL, "tracking E-W sines must be finite and within [-1, 1]");
+        jb.track_frames = nf;
+        jb.track.resize((size_t)r->n_chan * nf * kEw * kCyl);
+        for (int c = 0; c < r->n_chan; ++c)
+            for (int64_t F = 0; F < nf; ++F)
+                ew_phases(p, r->chan_freq_hz[c], r->ew_sin_frames + F * kEw,
+                          reinterpret_cast<float*>(jb.track.data() + ((size_t)c * nf + F) * kEw * kCyl));
+    }
     jb.ticket = p->next_ticket++;
     jb.req = *r;
+    jb.req.ew_sin_frames = nullptr;
     jb.freqs.assign(r->chan_freq_hz, r->chan_freq_hz + r->n_chan);
     jb.req.chan_freq_hz = jb.freqs.data();
     Ticket t;
@@ -699,8 +782,13 @@ int bf_destroy(bf_plan_t p) {
         for (auto& ib : p->inflight) {
             cudaEventDestroy(ib.ev);
             for (auto& r : ib.release) cudaFree(r.second);
+            if (ib.track.host) p->track_pool.emplace(ib.track.bytes, ib.track);
         }
         for (auto& kv : p->carry_pool) cudaFree(kv.second);
+        for (auto& kv : p->track_pool) {
+            cudaFreeHost(kv.second.host);
+            cudaFree(kv.second.dev);
+        }
         for (auto ev : p->event_pool) cudaEventDestroy(ev);
     }
     cudaFree(p->d_lut);

@@ -172,6 +172,28 @@ def config_node_slice(seed: int = 0, n_samples: int = 49152, freqs=None):
     return raw, np.array(freqs), {"burst_beam": 256 * j + m, "burst_chan": 2}
 
 
+def cylinder_quarter_turns(k_frames: Sequence[int], seed: int, frame: int = 384) -> np.ndarray:
+    """uint8 [len(k_frames) * frame, 2048]: random 4-bit values in [-7, 7] on
+    cylinder 0; cylinder c holds cylinder 0's values times i^(k_F c) during
+    frame F.  Multiplying by i maps the clipped 4-bit lattice onto itself, so
+    this is an exact plane wave whose E-W phase step between cylinders is k_F
+    quarter turns, changing from frame to frame (a source drifting in E-W)."""
+    rng = np.random.default_rng(seed)
+    T = len(k_frames) * frame
+    re = rng.integers(-7, 8, size=(T, N_FEED, 2), dtype=np.int16)
+    im = rng.integers(-7, 8, size=(T, N_FEED, 2), dtype=np.int16)
+    out_re = np.empty((T, N_CYL, N_FEED, 2), np.int16)
+    out_im = np.empty_like(out_re)
+    for F, k in enumerate(k_frames):
+        sl = slice(F * frame, (F + 1) * frame)
+        for c in range(N_CYL):
+            r, i = re[sl], im[sl]
+            for _ in range((int(k) * c) % 4):
+                r, i = -i, r
+            out_re[sl, c], out_im[sl, c] = r, i
+    return encode(out_re, out_im).reshape(T, N_INPUT)
+
+
 def noise_only(freqs_hz: Sequence[float], n_samples: int, seed: int, sigma: float = 2.5) -> np.ndarray:
     return make_voltages(freqs_hz, n_samples, seed, sigma=sigma)
 

@@ -417,3 +417,51 @@ def test_dedispersion_aligns_a_synthetic_sweep():
     assert series[5, t0] == 96 and series[5].sum() == 96
     flat, d0 = O.dedisperse(Oarr, freqs, 0.0)
     assert np.all(d0 == 0) and np.allclose(flat, Oarr.sum(axis=1))
+
+
+# --- tracking E-W beams (Sec. 3.1: static or tracking) ---------------------------------
+
+def quarter_turn_sines(freq, k_frames, D=20.0):
+    """E-W sine at which the cylinder phase step f D u / c0 is k/4 turns."""
+    return np.array([k * O.C0 / (4.0 * freq * D) for k in k_frames])
+
+
+def test_tracking_with_constant_table_is_static():
+    freq = 480e6
+    raw = rand_raw((384 * 2 + 40, 2048))
+    u = np.array([-0.3, 0.0, 0.1, 0.45])
+    ref = O.beamform_channel(raw, freq, ew_sin=u)
+    got = O.beamform_channel(raw, freq, ew_sin_frames=np.tile(u, (2, 1)))
+    assert np.allclose(got, ref, rtol=1e-12, atol=0)
+
+
+def test_tracking_beam_keeps_the_coherent_gain_of_a_drifting_source():
+    """Cylinder c carries cylinder 0 times i^(k_F c) in frame F (an exact
+    plane wave drifting in E-W).  A beam that tracks it adds the four
+    cylinders in phase: its power is 4^2 = 16 times the power of cylinder 0
+    alone, frame by frame; a static beam loses that gain once the source moves."""
+    freq = 600e6
+    k = [0, 1, 2, 3, 1]
+    raw = synth.cylinder_quarter_turns(k, seed=5)
+    only0 = raw.copy()
+    only0.reshape(-1, 4, 512)[:, 1:] = synth.encode(0, 0)
+    u = np.zeros((len(k), 4))
+    u[:, 0] = quarter_turn_sines(freq, k)
+    track = O.beamform_channel(raw, freq, ew_sin_frames=u)
+    single = O.beamform_channel(only0, freq, ew_sin_frames=u)
+    assert np.allclose(track[:256], 16.0 * single[:256], rtol=1e-10, atol=0)
+    static = O.beamform_channel(raw, freq, ew_sin=u[0])
+    for F in (1, 2, 3):
+        assert static[:256, :, F].sum() < 0.5 * track[:256, :, F].sum()
+    # beams 1..3 point at u = 0: a k = 2 (half-turn) step cancels in pairs
+    assert np.allclose(track[256:, :, 2], 0.0, atol=1e-9 * track[:256, :, 2].max())
+
+
+def test_tracking_rows_select_their_own_frame():
+    freq = 700e6
+    raw = rand_raw((384 * 3, 2048))
+    u = np.array([[0.0, 0.1, 0.2, 0.3], [0.05, -0.1, 0.25, -0.3], [0.5, 0.4, -0.2, 0.01]])
+    got = O.beamform_channel(raw, freq, ew_sin_frames=u)
+    for F in range(3):
+        one = O.beamform_channel(raw[384 * F:384 * (F + 1)], freq, ew_sin=u[F])
+        assert np.allclose(got[..., F], one[..., 0], rtol=1e-12, atol=0)
