@@ -40,10 +40,10 @@ constexpr int kWarps = kThreads / 32;       // 8: warp w loads row pair a = w
 constexpr int kPairs = kWarps / 2;
 
 // shared memory (float4 = one SoA pair: re0, re1, im0, im1)
-constexpr int kBinsF4 = kWarps * kBins;             // 8 row pairs x 512 bins
+constexpr int kBinsF4 = kWarps * kBins;             // 8 row pairs x 512 bins (one of two buffers)
 constexpr int kYscF4 = 2 * kFeed;                    // per warp pair: 2 row pairs x 256 feeds
 constexpr int kTbF4 = 2 * kFeed;                     // per warp: 2 row pairs x 16 x 16
-constexpr size_t kSmemBins = (size_t)kBinsF4 * 16;
+constexpr size_t kSmemBins = 2 * (size_t)kBinsF4 * 16;   // double-buffered across iterations
 constexpr size_t kSmemYsc = (size_t)kPairs * kYscF4 * 16;
 constexpr size_t kSmemTb = (size_t)kWarps * kTbF4 * 16;
 constexpr size_t kSmemLut = kNs * sizeof(int);
@@ -60,10 +60,30 @@ constexpr size_t kSmemTotal = kSmemBins + kSmemYsc + kSmemTb + kSmemLut + kSmemT
 // e = warp & 1: the half of the padded FFT this warp computes, and the slot
 // of the row pair it loads.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_sa(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// 128-bit shared-memory access by 32-bit shared address.  The XOR swizzles
+// below become one LOP3 with an immediate per access on top of a per-lane base.
+__device__ __forceinline__ void sts_cp(uint32_t addr, cp a) {
+    asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};"
+                 :: "r"(addr), "f"(a.re.x), "f"(a.re.y), "f"(a.im.x), "f"(a.im.y) : "memory");
+}
+__device__ __forceinline__ cp lds_cp(uint32_t addr) {
+    cp a;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(a.re.x), "=f"(a.re.y), "=f"(a.im.x), "=f"(a.im.y) : "r"(addr) : "memory");
+    return a;
+}
+
 __device__ __forceinline__ void phase_a(const uint4 (&in0)[kCyl], const uint4 (&in1)[kCyl], uint32_t sel,
-                                        const EwW& w, const PostTw& pt, float4* ysc, float4* tb, float4* bins2,
+                                        const EwW& w, const PostTw& pt, uint32_t ysc, uint32_t tb, uint32_t bins2,
                                         int e, int lane, int bar_id) {
-    // unpack + E-W: lane holds feeds 8 lane .. 8 lane + 7 of both rows
+    // unpack + E-W: lane holds feeds 8 lane .. 8 lane + 7 of both rows.  Feed n = 8 lane + 2k (+1)
+    // sits at n2 = n & 15 = 8 (lane & 1) + 2k (+1), n1 = n >> 4 = lane >> 1; ysw(n2, n1) =
+    // 16 n2 + (n1 ^ (n2 & 7) ^ 4 (n2 >> 3)) = 16 n2 + (((lane >> 1) ^ 4 (lane & 1)) ^ (n2 & 7)).
+    const uint32_t yw = ysc + 16u * (uint32_t)(e * kFeed + 16 * 8 * (lane & 1) + (((lane >> 1) ^ (4 * (lane & 1)))));
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         cp yA, yB;
@@ -83,18 +103,19 @@ __device__ __forceinline__ void phase_a(const uint4 (&in0)[kCyl], const uint4 (&
                 yB.im = fma2(xrB, w.I[c - 1], fma2(xiB, w.R[c - 1], yB.im));
             }
         }
-        // feed n = 8 lane + 2k (+1): n2 = n & 15, n1 = n >> 4
-        const int n2 = ((lane & 1) << 3) | (2 * k), n1 = lane >> 1;
-        st_cp(ysc + e * kFeed + ysw(n2, n1), yA);
-        st_cp(ysc + e * kFeed + ysw(n2 + 1, n1), yB);
+        // rows n2 = 2k and 2k + 1 of this lane's half: + 256 n2 bytes, low slot bits ^ n2
+        sts_cp((yw ^ (uint32_t)(16 * (2 * k))) + 256u * (2 * k), yA);
+        sts_cp((yw ^ (uint32_t)(16 * (2 * k + 1))) + 256u * (2 * k + 1), yB);
     }
     pair_sync(bar_id);
 
-    // lanes 0-15: row pair slot 0, lanes 16-31: slot 1; lane handles n2
+    // lanes 0-15: row pair slot 0, lanes 16-31: slot 1; lane handles n2:
+    // ysw(n2, n1) = 16 n2 + (n1 ^ f), f = (n2 & 7) ^ 4 (n2 >> 3)
     const int rp = lane >> 4, n2 = lane & 15;
+    const uint32_t yr = ysc + 16u * (uint32_t)(rp * kFeed + 16 * n2 + ((n2 & 7) ^ (4 * (n2 >> 3))));
     cp v[16];
 #pragma unroll
-    for (int n1 = 0; n1 < 16; ++n1) v[n1] = ld_cp(ysc + rp * kFeed + ysw(n2, n1));
+    for (int n1 = 0; n1 < 16; ++n1) v[n1] = lds_cp(yr ^ (uint32_t)(16 * n1));
     if (e) {
         // odd bins: input times exp(-i pi n / 256) = exp(-2 pi i n1 / 32) * exp(-2 pi i n2 / 512);
         // the second factor is folded into the per-lane twiddles
@@ -104,17 +125,26 @@ __device__ __forceinline__ void phase_a(const uint4 (&in0)[kCyl], const uint4 (&
     dft16(v);
 #pragma unroll
     for (int k1 = 0; k1 < 16; ++k1) v[k1] = cmulp(v[k1], pt.C[k1], pt.S[k1]);
+    // transpose through tb: tsw(r, c) = 16 r + (c ^ (r & 7))
+    const uint32_t tbl = tb + 16u * (uint32_t)(rp * kFeed);
+    {
+        const uint32_t tw_ = tbl + 256u * (uint32_t)n2 + 16u * (uint32_t)(n2 & 7);
 #pragma unroll
-    for (int k1 = 0; k1 < 16; ++k1) st_cp(tb + rp * kFeed + tsw(n2, k1), v[k1]);
+        for (int k1 = 0; k1 < 16; ++k1) sts_cp(tw_ ^ (uint32_t)(16 * k1), v[k1]);
+    }
     __syncwarp();
     const int k1 = n2;
+    {
+        const uint32_t tr_ = tbl + 16u * (uint32_t)k1;
 #pragma unroll
-    for (int r = 0; r < 16; ++r) v[r] = ld_cp(tb + rp * kFeed + tsw(r, k1));
+        for (int r = 0; r < 16; ++r) v[r] = lds_cp((tr_ ^ (uint32_t)(16 * (r & 7))) + 256u * r);
+    }
     dft16(v);
-    // bin of the 512-point padded FFT: L = 2 (k1 + 16 k2) + e
-    float4* row = bins2 + rp * kBins;
+    // bin of the 512-point padded FFT: L = 2 (k1 + 16 k2) + e = 32 k2 + (2 k1 + e), and
+    // bsw(L) = 32 k2 + bsw(2 k1 + e) because bit 3 of L does not depend on k2
+    const uint32_t row = bins2 + 16u * (uint32_t)(rp * kBins + bsw(2 * k1 + e));
 #pragma unroll
-    for (int k2 = 0; k2 < 16; ++k2) st_cp(row + bsw(2 * (k1 + 16 * k2) + e), v[k2]);
+    for (int k2 = 0; k2 < 16; ++k2) sts_cp(row + 16u * 32u * k2, v[k2]);
 }
 
 // ---------------------------------------------------------------------------
@@ -122,8 +152,8 @@ __device__ __forceinline__ void phase_a(const uint4 (&in0)[kCyl], const uint4 (&
 // ---------------------------------------------------------------------------
 template <bool kDump>
 __global__ void __launch_bounds__(kThreads, 1) fused_fp32_kernel(const __grid_constant__ Batch bt) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    float4* bins = reinterpret_cast<float4*>(smem);
+    extern __shared__ __align__(256) unsigned char smem[];   // the swizzles XOR address bits 4-7
+    float4* bins_all = reinterpret_cast<float4*>(smem);
     float4* ysc_all = reinterpret_cast<float4*>(smem + kSmemBins);
     float4* tb_all = reinterpret_cast<float4*>(smem + kSmemBins + kSmemYsc);
     int* lut_s = reinterpret_cast<int*>(smem + kSmemBins + kSmemYsc + kSmemTb);
@@ -132,9 +162,9 @@ __global__ void __launch_bounds__(kThreads, 1) fused_fp32_kernel(const __grid_co
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int e = warp & 1, q = warp >> 1;
-    float4* ysc = ysc_all + q * kYscF4;
-    float4* tb = tb_all + warp * kTbF4;
-    float4* bins2 = bins + (2 * q) * kBins;
+    const uint32_t ysc_sa = smem_sa(ysc_all + q * kYscF4);
+    const uint32_t tb_sa = smem_sa(tb_all + warp * kTbF4);
+
 
     // gather / second pass role: TMEM lane quarter = warp & 3, bin half = warp >> 2
     const int ell = 32 * (warp & 3) + lane;
@@ -160,6 +190,7 @@ __global__ void __launch_bounds__(kThreads, 1) fused_fp32_kernel(const __grid_co
     PostTw pt;
     load_post(bt.tw512, lane & 15, e, pt);
 
+    int par = 0;                     // bins buffer of the next iteration
     for (int item = blockIdx.x; item < bt.n_items; item += gridDim.x) {
         int sgi = 0;
         while (sgi + 1 < bt.n_segs && bt.segs[sgi + 1].item_begin <= item) ++sgi;
@@ -178,15 +209,17 @@ __global__ void __launch_bounds__(kThreads, 1) fused_fp32_kernel(const __grid_co
         for (int s = 0; s < kSub; ++s) acc[s] = make_float2(0.f, 0.f);
 
         const long long row0 = (long long)F * kFrame;
-        uint4 cur0[kCyl], cur1[kCyl];
-        load_row(frame_row(sg, row0 + 16 * warp), lane, cur0);
-        load_row(frame_row(sg, row0 + 16 * warp + 1), lane, cur1);
+        // raw rows of the current iteration and the prefetched next one; the loop body is
+        // unrolled twice with the roles swapped so the rows are never copied
+        uint4 ra0[kCyl], ra1[kCyl], rb0[kCyl], rb1[kCyl];
+        load_row(frame_row(sg, row0 + 16 * warp), lane, ra0);
+        load_row(frame_row(sg, row0 + 16 * warp + 1), lane, ra1);
 
         for (int ps = 0; ps < kTds * kPol; ++ps) {
             const int blk = ps >> 1, pol = ps & 1;
             const uint32_t sel = 0x4400u | ((2u + pol) << 4) | (uint32_t)pol;
-            for (int it = 0; it < 8; ++it) {
-                uint4 nxt0[kCyl], nxt1[kCyl];
+            auto step = [&](int it, const uint4 (&cur0)[kCyl], const uint4 (&cur1)[kCyl], uint4 (&nxt0)[kCyl],
+                            uint4 (&nxt1)[kCyl]) {
                 const bool more = it < 7 || ps + 1 < kTds * kPol;
                 if (more) {
                     const int nit = it < 7 ? it + 1 : 0;
@@ -195,32 +228,32 @@ __global__ void __launch_bounds__(kThreads, 1) fused_fp32_kernel(const __grid_co
                     load_row(frame_row(sg, r), lane, nxt0);
                     load_row(frame_row(sg, r + 1), lane, nxt1);
                 }
-                phase_a(cur0, cur1, sel, w, pt, ysc, tb, bins2, e, lane, 1 + q);
+                // bins of this iteration: one buffer while the other is still being gathered
+                float4* bins = bins_all + par * kBinsF4;
+                par ^= 1;
+                phase_a(cur0, cur1, sel, w, pt, ysc_sa, tb_sa, smem_sa(bins + (2 * q) * kBins), e, lane, 1 + q);
                 cta_sync();
                 // gather + 8-point DFT over a (tau = 16 a + b, b = 2 it, 2 it + 1)
-                {
-                    cp z[8];
+                cp z[8];
 #pragma unroll
-                    for (int a = 0; a < 8; ++a) z[a] = ld_cp(bins + a * kBins + Lsw);
-                    dft8(z);
-                    const int b0 = 2 * it;
+                for (int a = 0; a < 8; ++a) z[a] = ld_cp(bins + a * kBins + Lsw);
+                dft8(z);
+                const int b0 = 2 * it;
 #pragma unroll
-                    for (int c = 0; c < 8; ++c) {
-                        if (c) {
-                            const float4 t = tw_s[it * 8 + c];
-                            z[c] = cmulp(z[c], make_float2(t.x, t.y), make_float2(t.z, t.w));
-                        }
-                        tmem_st4(tlane + hh * 256 + 2 * (16 * c + b0), z[c].re.x, z[c].im.x, z[c].re.y, z[c].im.y);
+                for (int c = 0; c < 8; ++c) {
+                    if (c) {
+                        const float4 t = tw_s[it * 8 + c];
+                        z[c] = cmulp(z[c], make_float2(t.x, t.y), make_float2(t.z, t.w));
                     }
+                    tmem_st4(tlane + hh * 256 + 2 * (16 * c + b0), z[c].re.x, z[c].im.x, z[c].re.y, z[c].im.y);
                 }
-                cta_sync();
-                if (more) {
-#pragma unroll
-                    for (int c = 0; c < kCyl; ++c) {
-                        cur0[c] = nxt0[c];
-                        cur1[c] = nxt1[c];
-                    }
-                }
+                // no barrier here: the next iteration writes the other bins buffer, and the
+                // barrier after its phase A orders this gather before the buffer's reuse
+            };
+#pragma unroll 1
+            for (int it = 0; it < 8; it += 2) {
+                step(it, ra0, ra1, rb0, rb1);
+                step(it + 1, rb0, rb1, ra0, ra1);
             }
             tmem_wait_st();
             cta_sync();
@@ -254,9 +287,9 @@ __global__ void __launch_bounds__(64) debug_beams_kernel(const uint8_t* __restri
                                                           const int16_t* __restrict__ lut,
                                                           const float2* __restrict__ ew, const float2* __restrict__ tw512,
                                                           float2* __restrict__ out) {
-    __shared__ float4 ysc[kYscF4];
-    __shared__ float4 tbs[2][kTbF4];
-    __shared__ float4 bins2[2 * kBins];
+    __shared__ __align__(256) float4 ysc[kYscF4];         // 256-byte rows: the swizzles XOR address bits 4-7
+    __shared__ __align__(256) float4 tbs[2][kTbF4];
+    __shared__ __align__(256) float4 bins2[2 * kBins];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, e = warp;
     const long long t0 = (long long)blockIdx.x * 4;
     const int pol = blockIdx.y & 1, j = blockIdx.y >> 1;
@@ -269,7 +302,7 @@ __global__ void __launch_bounds__(64) debug_beams_kernel(const uint8_t* __restri
     load_row(vin + ra * kInput, lane, in0);
     load_row(vin + rb * kInput, lane, in1);
     const uint32_t sel = 0x4400u | ((2u + pol) << 4) | (uint32_t)pol;
-    phase_a(in0, in1, sel, w, pt, ysc, tbs[warp], bins2, e, lane, 1);
+    phase_a(in0, in1, sel, w, pt, smem_sa(ysc), smem_sa(tbs[warp]), smem_sa(bins2), e, lane, 1);
     __syncthreads();
     for (int i = threadIdx.x; i < 4 * kNs; i += 64) {
         const int r = i >> 8, mm = i & 255;          // r: row 0..3 = slot (r >> 1), element (r & 1)
