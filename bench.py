@@ -258,6 +258,28 @@ def cpu_baseline(raw, freqs, gpu_out=None, form_outs=None, frames_per_chan: int 
     return res
 
 
+def oracle_one_core(raw, freqs, frames_per_chan: int = 1):
+    """The oracle on one host core: a child process with single-threaded BLAS
+    (the thread count is fixed when numpy loads, so it cannot change here)."""
+    import subprocess
+    import tempfile
+    T = frames_per_chan * 384
+    with tempfile.TemporaryDirectory() as td:
+        path = os.path.join(td, "raw.npy")
+        np.save(path, np.ascontiguousarray(raw[:, :T]))
+        env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+        code = ("import sys, time, numpy as np; sys.path.insert(0, %r); import oracle.chime_fftbf as O; "
+                "raw = np.load(%r); O.beamform(raw[:, :384], %r); t0 = time.perf_counter(); "
+                "O.beamform(raw, %r); print(time.perf_counter() - t0)") % (ROOT, path, list(freqs), list(freqs))
+        r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
+    if r.returncode != 0:
+        return {"error": r.stderr.strip().splitlines()[-1] if r.stderr.strip() else "failed"}
+    dt = float(r.stdout.strip().splitlines()[-1])
+    return {"value": N_CHAN * T * N_INPUT / dt, "unit": "input-samples/s", "cores": 1,
+            "sample": f"first {frames_per_chan} frame(s) of each of the {N_CHAN} channels, single-threaded BLAS, "
+                      f"{dt:.1f} s"}
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -508,6 +530,7 @@ def main():
                                                form=headline_form))
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(raw, freqs, host_out.numpy(), form_outs)
+            line["cpu_baseline"]["one_core"] = oracle_one_core(raw, freqs)
         print(json.dumps(line), flush=True)
     plan.close()
     if ws > 1:
