@@ -208,6 +208,17 @@ int bf_debug_tables(const bf_config* cfg, double freq_hz, int32_t* lut_out, floa
  * float2 [block][pol][ew][ns][t], t = 0..127, for n_samples a multiple of 384. */
 int bf_debug_gemm(bf_plan_t p, double freq_hz, const uint8_t* d_vin, int64_t n_samples, float* d_out);
 
+/* Failure-detection check of the device-side waits (no counterpart in the
+ * paper): runs the tensor-core kernel on one frame (d_vin: device, 384 x 2048
+ * bytes, 16-byte aligned) with its MMA warp idle, so no pipeline stage is ever
+ * released, and every mbarrier wait bounded by wait_ns (1 .. 2e9).  The
+ * kernel neither traps nor spins unbounded: its waits run out, it frees its
+ * tensor memory and reports through the plan's status word, and the call
+ * returns BF_ETIMEDOUT, after which the plan and the CUDA context remain
+ * usable.  BF_OK would mean a wait did not expire.  Any plan form may call it;
+ * it synchronises the plan's stream. */
+int bf_debug_stall(bf_plan_t p, const uint8_t* d_vin, int64_t wait_ns);
+
 /* Device unpack of n bytes into 2n floats (re, im), with the same device
  * code the fused kernel uses.  d_in, d_out device pointers. */
 int bf_debug_unpack(bf_plan_t p, const uint8_t* d_in, float* d_out, int64_t n);

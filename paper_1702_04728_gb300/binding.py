@@ -24,7 +24,7 @@ N_BEAMS, N_SUB, FRAME, N_INPUT = 1024, 16, 384, 2048
 
 SYMBOLS = ["bf_config_default", "bf_plan", "bf_frames_out", "bf_submit", "bf_poll", "bf_destroy",
            "bf_last_error", "bf_skymap", "bf_rescale_u8", "bf_dedisperse", "bf_debug_tables", "bf_debug_gemm", "bf_debug_unpack", "bf_debug_beams",
-           "bf_debug_upchan"]
+           "bf_debug_upchan", "bf_debug_stall"]
 
 
 class BfError(RuntimeError):
@@ -77,6 +77,7 @@ def lib() -> ctypes.CDLL:
         L.bf_debug_beams.argtypes = [P, D, P, I64, P]
         L.bf_debug_upchan.argtypes = [P, D, P, I64, P]
         L.bf_debug_gemm.argtypes = [P, D, P, I64, P]
+        L.bf_debug_stall.argtypes = [P, P, I64]
         L.bf_skymap.argtypes = [P, P, I64, I64, P]
         L.bf_rescale_u8.argtypes = [P, P, I64, I64, P, P]
         L.bf_dedisperse.argtypes = [P, P, I, ctypes.POINTER(D), I64, D, P, ctypes.POINTER(I64)]
@@ -204,6 +205,11 @@ def bf_debug_upchan(plan: int, freq_hz: float, d_vin, n_samples: int, d_out) -> 
 
 def bf_debug_gemm(plan: int, freq_hz: float, d_vin, n_samples: int, d_out) -> None:
     _check(lib().bf_debug_gemm(plan, float(freq_hz), _ptr(d_vin), n_samples, _ptr(d_out)))
+
+
+def bf_debug_stall(plan: int, d_vin, wait_ns: int) -> int:
+    """Returns the status code as is (BF_ETIMEDOUT is the expected outcome)."""
+    return int(lib().bf_debug_stall(plan, _ptr(d_vin), int(wait_ns)))
 
 
 def bf_skymap(plan: int, d_out, n_sub: int, n_frames: int, d_map) -> None:

@@ -52,6 +52,7 @@ struct Batch {
     const unsigned char* a_tc;   // tensor-core form: FP16 twiddle images per table
     size_t a_tc_stride;          // bytes per table in a_tc
     int* status;                 // set non-zero by a kernel whose bounded wait expired
+    unsigned long long wait_ns;  // bound on each device-side wait (0: the default, 2 s)
     Seg segs[kMaxSegs];
 };
 
@@ -64,7 +65,9 @@ cudaError_t debug_unpack_launch(const uint8_t* in, float* out, long long n, cuda
 int fused_fp32_max_grid(int device);   // CTAs that fit at once (1 per SM)
 
 // Tensor-core form: `terms` = 1, 2 or 3 GEMM terms; mode 0 = detect,
-// 1 = dump up-channelised voltages, 2 = dump the N-S/E-W beams of the GEMM.
+// 1 = dump up-channelised voltages, 2 = dump the N-S/E-W beams of the GEMM,
+// 3 = stall check (1 term only): the MMA warp stays idle, so the producers'
+// bounded waits run out and the kernel reports through `status`.
 cudaError_t fused_tc_launch(const Batch& b, int terms, int mode, int grid, cudaStream_t s);
 size_t tc_a_bytes(int terms);    // bytes of one table's twiddle image(s)
 cudaError_t skymap_launch(const float* in, int n_beams, long long per_beam, float* map, cudaStream_t s);

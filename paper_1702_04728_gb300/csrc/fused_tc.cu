@@ -92,8 +92,9 @@ __device__ __forceinline__ unsigned long long globaltimer() {
     return t;
 }
 
-// Bounded wait for the completion of phase `parity` of an mbarrier.
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+// Bounded wait for the completion of phase `parity` of an mbarrier: false once
+// `limit` ns have passed without it.
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, unsigned long long limit) {
     const unsigned long long t0 = globaltimer();
     for (;;) {
         uint32_t ok;
@@ -103,7 +104,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
             "selp.u32 %0, 1, 0, p;\n\t}"
             : "=r"(ok) : "r"(mbar), "r"(parity) : "memory");
         if (ok) return true;
-        if (globaltimer() - t0 > kWaitNs) return false;
+        if (globaltimer() - t0 > limit) return false;
     }
 }
 
@@ -327,7 +328,8 @@ __device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
 }
 
 // MODE: 0 = detect and integrate, 1 = dump up-channelised voltages,
-//       2 = dump the N-S/E-W beams of the GEMM (stage dump).
+//       2 = dump the N-S/E-W beams of the GEMM (stage dump), 3 = stall check
+//       (the MMA warp stays idle; the producers' bounded waits must run out).
 //
 // Warps 0-7 produce B chunks and run the up-channel passes out of TMEM; warp 8
 // streams the twiddle chunks (bulk copies, NA-deep ring) and issues the MMAs.
@@ -389,10 +391,12 @@ __global__ void __launch_bounds__(TcCfg<TERMS>::NT, 1) fused_tc_kernel(const __g
     cta_sync();
     const uint32_t tmem = tmem_base_s;
     constexpr int PASSES = kTds * kPol;
+    const unsigned long long wlim = bt.wait_ns ? bt.wait_ns : kWaitNs;
 
     if (!producer) {
         // ------------------------------ MMA / copy warp ------------------------------
-        if (lane == 0) {
+        // (MODE 3, the stall check: this warp stays idle, so no chunk is ever consumed)
+        if (lane == 0 && MODE != 3) {
             uint32_t p_bfull = 0, p_afull = 0, p_aempty = 0, p_tfree = 0;
             long long c = 0;                                  // global chunk number
             long long c_copy = 0;                             // next twiddle chunk to copy
@@ -424,12 +428,12 @@ __global__ void __launch_bounds__(TcCfg<TERMS>::NT, 1) fused_tc_kernel(const __g
                 const int s = (int)(c & 1), a = (int)(c % NA), kc = (int)(c % C::NCH);
                 if (kc == 0 && c > 0) {
                     // the previous pass's accumulator has been read by the producers
-                    if (!mbar_wait(tfree, p_tfree)) ok = false;
+                    if (!mbar_wait(tfree, p_tfree, wlim)) ok = false;
                     p_tfree ^= 1u;
                 }
-                if (!mbar_wait(bfull(s), (p_bfull >> s) & 1u)) ok = false;
+                if (!mbar_wait(bfull(s), (p_bfull >> s) & 1u, wlim)) ok = false;
                 p_bfull ^= 1u << s;
-                if (!mbar_wait(afull(a), (p_afull >> a) & 1u)) ok = false;
+                if (!mbar_wait(afull(a), (p_afull >> a) & 1u, wlim)) ok = false;
                 p_afull ^= 1u << a;
                 if (!ok) break;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -455,7 +459,7 @@ __global__ void __launch_bounds__(TcCfg<TERMS>::NT, 1) fused_tc_kernel(const __g
                 if (c_copy < total) {
                     if (c_copy >= NA) {
                         const int ra = (int)(c_copy % NA);
-                        if (!mbar_wait(aempty(ra), (p_aempty >> ra) & 1u)) ok = false;
+                        if (!mbar_wait(aempty(ra), (p_aempty >> ra) & 1u, wlim)) ok = false;
                         p_aempty ^= 1u << ra;
                     }
                     issue_copy(c_copy);
@@ -491,7 +495,7 @@ __global__ void __launch_bounds__(TcCfg<TERMS>::NT, 1) fused_tc_kernel(const __g
                 for (int kc = 0; kc < C::NCH && ok; ++kc, ++c) {
                     const int s = (int)(c & 1);
                     if (c >= 2) {
-                        if (!mbar_wait(bempty(s), (p_bempty >> s) & 1u)) ok = false;
+                        if (!mbar_wait(bempty(s), (p_bempty >> s) & 1u, wlim)) ok = false;
                         p_bempty ^= 1u << s;
                     }
                     unsigned char* sb_hi = b_ring + s * C::B_STAGE;
@@ -509,7 +513,7 @@ __global__ void __launch_bounds__(TcCfg<TERMS>::NT, 1) fused_tc_kernel(const __g
                     if (abort_s) ok = false;
                 }
                 if (!ok) break;
-                if (!mbar_wait(accfull, p_acc)) ok = false;
+                if (!mbar_wait(accfull, p_acc, wlim)) ok = false;
                 p_acc ^= 1u;
                 if (!ok) break;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -576,6 +580,7 @@ cudaError_t fused_tc_launch(const Batch& b, int terms, int mode, int grid, cudaS
         case 10: return launch_tc<1, 0>(b, grid, s);
         case 11: return launch_tc<1, 1>(b, grid, s);
         case 12: return launch_tc<1, 2>(b, grid, s);
+        case 13: return launch_tc<1, 3>(b, grid, s);
         case 20: return launch_tc<2, 0>(b, grid, s);
         case 21: return launch_tc<2, 1>(b, grid, s);
         case 22: return launch_tc<2, 2>(b, grid, s);

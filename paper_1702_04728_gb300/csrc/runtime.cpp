@@ -945,4 +945,28 @@ int bf_debug_gemm(bf_plan_t p, double freq_hz, const uint8_t* d_vin, int64_t n_s
     return debug_fused(p, freq_hz, d_vin, n_samples, d_out, 2);
 }
 
+int bf_debug_stall(bf_plan_t p, const uint8_t* d_vin, int64_t wait_ns) {
+    if (!p || !d_vin || wait_ns <= 0 || wait_ns > 2000000000LL) return fail(BF_EINVAL, "bad argument");
+    if (((uintptr_t)d_vin & 15) != 0) return fail(BF_EINVAL, "vin must be 16-byte aligned");
+    CK(cudaSetDevice(p->device));
+    Batch b = make_batch(p);
+    {
+        std::lock_guard<std::mutex> lk(p->mu);
+        int rc = table_for(p, 600e6, &b.segs[0].table);
+        if (rc) return rc;
+    }
+    b.n_segs = 1;
+    b.n_items = kEw;                       // one frame, four E-W beams
+    b.segs[0].vin = d_vin;
+    b.segs[0].n_frames = 1;
+    b.wait_ns = (unsigned long long)wait_ns;
+    CK(fused_tc_launch(b, 1, 3, std::min(p->grid, kEw), p->stream));
+    CK(cudaStreamSynchronize(p->stream));
+    if (p->h_status && *(volatile int*)p->h_status) {
+        *(volatile int*)p->h_status = 0;
+        return fail(BF_ETIMEDOUT, "a bounded device-side wait expired (expected in the stall check)");
+    }
+    return BF_OK;
+}
+
 }  // extern "C"
