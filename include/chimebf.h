@@ -184,6 +184,26 @@ int bf_dedisperse(bf_plan_t p, const float* d_out, int n_chan, const double* cha
                   double dm, float* d_series, int64_t* n_out);
 
 /*
+ * bf_dedisperse without any device allocation (the paper has no counterpart:
+ * this serves callers that may not allocate, e.g. around CUDA graph capture).
+ * Same arguments, rule and result as bf_dedisperse, for n_chan <= 4096 (at
+ * most 65536 sub-channels; more is rejected with BF_EINVAL before any work).
+ * The delay table lives in one file-scope device array of 65536 ints
+ * (256 KB) per device:
+ *   - the array is shared by every plan and thread of the process on that
+ *     device, so overlapping calls (other streams or threads) race on it;
+ *   - it keeps the last call's delays; nothing in it has to start at zero,
+ *     because each call writes the n_chan * 16 entries it reads before its
+ *     kernel runs (in stream order on the plan's stream);
+ *   - the first call on a device looks the array's address up
+ *     (cudaGetSymbolAddress, device current, return code checked): make that
+ *     first call before any stream capture that includes this entry point.
+ * No cudaMalloc, cudaFree or other allocating call is made.
+ */
+int bf_dedisperse_static(bf_plan_t p, const float* d_out, int n_chan, const double* chan_freq_hz,
+                         int64_t n_frames, double dm, float* d_series, int64_t* n_out);
+
+/*
  * 8-bit intensity (Table 1 lists 8-bit integer output; the paper gives no
  * scaling rule).  For each of n_rows rows of n_frames floats (a bf_submit
  * output viewed as [1024 * n_sub][n_frames]): mean and standard deviation over

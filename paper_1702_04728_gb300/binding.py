@@ -24,7 +24,7 @@ N_BEAMS, N_SUB, FRAME, N_INPUT = 1024, 16, 384, 2048
 
 SYMBOLS = ["bf_config_default", "bf_plan", "bf_frames_out", "bf_submit", "bf_poll", "bf_destroy",
            "bf_last_error", "bf_skymap", "bf_rescale_u8", "bf_dedisperse", "bf_debug_tables", "bf_debug_gemm", "bf_debug_unpack", "bf_debug_beams",
-           "bf_debug_upchan", "bf_debug_stall"]
+           "bf_debug_upchan", "bf_debug_stall", "bf_dedisperse_static"]
 
 
 class BfError(RuntimeError):
@@ -81,6 +81,7 @@ def lib() -> ctypes.CDLL:
         L.bf_skymap.argtypes = [P, P, I64, I64, P]
         L.bf_rescale_u8.argtypes = [P, P, I64, I64, P, P]
         L.bf_dedisperse.argtypes = [P, P, I, ctypes.POINTER(D), I64, D, P, ctypes.POINTER(I64)]
+        L.bf_dedisperse_static.argtypes = [P, P, I, ctypes.POINTER(D), I64, D, P, ctypes.POINTER(I64)]
         for name in SYMBOLS:
             getattr(L, name).restype = ctypes.c_char_p if name == "bf_last_error" else I
         _lib = L
@@ -222,6 +223,16 @@ def bf_dedisperse(plan: int, d_out, freqs, n_frames: int, dm: float, d_series) -
     n = ctypes.c_int64()
     _check(lib().bf_dedisperse(plan, _ptr(d_out), len(freqs), fptr, n_frames, float(dm), _ptr(d_series),
                                ctypes.byref(n)))
+    del farr
+    return n.value
+
+
+def bf_dedisperse_static(plan: int, d_out, freqs, n_frames: int, dm: float, d_series) -> int:
+    """As bf_dedisperse, with the delay table in the library's static device array."""
+    fptr, farr = _dbl_array(list(freqs))
+    n = ctypes.c_int64()
+    _check(lib().bf_dedisperse_static(plan, _ptr(d_out), len(freqs), fptr, n_frames, float(dm), _ptr(d_series),
+                                      ctypes.byref(n)))
     del farr
     return n.value
 

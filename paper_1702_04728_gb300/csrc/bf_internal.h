@@ -73,6 +73,11 @@ size_t tc_a_bytes(int terms);    // bytes of one table's twiddle image(s)
 cudaError_t skymap_launch(const float* in, int n_beams, long long per_beam, float* map, cudaStream_t s);
 cudaError_t dedisperse_launch(const float* in, const int* delays, int n_sub, long long nf, long long n_out,
                               float* out, cudaStream_t s);
+// Allocation-free dedispersion: the device's static delay table (address
+// looked up once per device; the caller has made `device` current).
+constexpr int kDdStaticMaxSub = kSub * 4096;    // 4096 channels x 16 sub-channels
+constexpr int kMaxDevices = 64;
+cudaError_t dedisperse_static_table(int device, int** table);
 cudaError_t rescale_u8_launch(const float* in, long long rows, long long nf, uint8_t* codes, float* stats,
                               cudaStream_t s);
 int tc_chunk_k(int terms);       // K elements per shared-memory chunk

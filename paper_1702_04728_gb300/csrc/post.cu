@@ -4,6 +4,7 @@
 #include "bf_internal.h"
 
 #include <cstdint>
+#include <mutex>
 
 namespace chimebf {
 namespace {
@@ -106,7 +107,27 @@ __global__ void dedisperse_kernel(const float* __restrict__ in, const int* __res
     out[(long long)beam * n_out + t] = acc;
 }
 
+// Delay table of the allocation-free dedispersion entry point: one array per
+// device, shared by every plan of the process (see bf_dedisperse_static).
+__device__ __align__(256) int g_dd_delays[kDdStaticMaxSub];
+
 }  // namespace
+
+cudaError_t dedisperse_static_table(int device, int** table) {
+    static std::mutex mu;
+    static int* ptrs[kMaxDevices] = {};
+    if (device < 0 || device >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!ptrs[device]) {
+        // once per device, with that device current (the caller has set it)
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_dd_delays);
+        if (e != cudaSuccess) return e;
+        ptrs[device] = static_cast<int*>(p);
+    }
+    *table = ptrs[device];
+    return cudaSuccess;
+}
 
 cudaError_t dedisperse_launch(const float* in, const int* delays, int n_sub, long long nf, long long n_out,
                               float* out, cudaStream_t s) {

@@ -813,30 +813,47 @@ int bf_skymap(bf_plan_t p, const float* d_out, int64_t n_sub, int64_t n_frames, 
     return BF_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// Dedispersion delays in frames of every sub-channel (rule of bf_dedisperse);
+// d must hold kSub * n_chan entries.  Returns BF_OK or BF_EINVAL.
+int dedisperse_delays(int n_chan, const double* chan_freq_hz, double dm, int* d, int* dmax_out) {
+    const int n_sub = kSub * n_chan;
+    const double fine = 390625.0 / kUp;
+    double fmax = 0.0;
+    for (int c = 0; c < n_chan; ++c) {
+        if (!(chan_freq_hz[c] > 0) || !std::isfinite(chan_freq_hz[c])) return fail(BF_EINVAL, "bad frequency");
+        for (int s = 0; s < kSub; ++s)
+            fmax = std::max(fmax, (chan_freq_hz[c] + (kFds * s + (kFds - 1) / 2.0 - kUp / 2) * fine) / 1e6);
+    }
+    int dmax = 0;
+    for (int i = 0; i < n_sub; ++i) {
+        const int c = i / kSub, s = i % kSub;
+        const double f = (chan_freq_hz[c] + (kFds * s + (kFds - 1) / 2.0 - kUp / 2) * fine) / 1e6;
+        const double x = ((4.148808e3 * dm) * (1.0 / (f * f) - 1.0 / (fmax * fmax))) / (kFrame * 2.56e-6);
+        d[i] = (int)std::floor(x + 0.5);
+        dmax = std::max(dmax, d[i]);
+    }
+    *dmax_out = dmax;
+    return BF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 int bf_dedisperse(bf_plan_t p, const float* d_out, int n_chan, const double* chan_freq_hz, int64_t n_frames,
                   double dm, float* d_series, int64_t* n_out) {
     if (!p || n_chan <= 0 || n_chan > 4096 || !chan_freq_hz || n_frames < 0 || !n_out || !(dm >= 0) ||
         !std::isfinite(dm))
         return fail(BF_EINVAL, "bad argument");
     const int n_sub = kSub * n_chan;
-    const double fine = 390625.0 / kUp;
-    std::vector<double> fs(n_sub);
-    double fmax = 0.0;
-    for (int c = 0; c < n_chan; ++c) {
-        if (!(chan_freq_hz[c] > 0) || !std::isfinite(chan_freq_hz[c])) return fail(BF_EINVAL, "bad frequency");
-        for (int s = 0; s < kSub; ++s) {
-            const double f = (chan_freq_hz[c] + (kFds * s + (kFds - 1) / 2.0 - kUp / 2) * fine) / 1e6;
-            fs[c * kSub + s] = f;
-            fmax = std::max(fmax, f);
-        }
-    }
     std::vector<int> d(n_sub);
     int dmax = 0;
-    for (int i = 0; i < n_sub; ++i) {
-        const double x = ((4.148808e3 * dm) * (1.0 / (fs[i] * fs[i]) - 1.0 / (fmax * fmax))) / (kFrame * 2.56e-6);
-        d[i] = (int)std::floor(x + 0.5);
-        dmax = std::max(dmax, d[i]);
-    }
+    int rc = dedisperse_delays(n_chan, chan_freq_hz, dm, d.data(), &dmax);
+    if (rc) return rc;
     *n_out = std::max<int64_t>(0, n_frames - dmax);
     if (*n_out == 0) return BF_OK;
     if (!d_out || !d_series) return fail(BF_EINVAL, "null buffer");
@@ -853,6 +870,29 @@ int bf_dedisperse(bf_plan_t p, const float* d_out, int n_chan, const double* cha
     CK(dedisperse_launch(d_out, p->d_delays, n_sub, (long long)n_frames, (long long)*n_out, d_series, p->stream));
     return BF_OK;
 }
+
+int bf_dedisperse_static(bf_plan_t p, const float* d_out, int n_chan, const double* chan_freq_hz,
+                         int64_t n_frames, double dm, float* d_series, int64_t* n_out) {
+    if (!p || n_chan <= 0 || !chan_freq_hz || n_frames < 0 || !n_out || !(dm >= 0) || !std::isfinite(dm))
+        return fail(BF_EINVAL, "bad argument");
+    if (kSub * n_chan > kDdStaticMaxSub)
+        return fail(BF_EINVAL, "more channels than the static delay table holds (4096 channels, 65536 sub-channels)");
+    const int n_sub = kSub * n_chan;
+    std::vector<int> d(n_sub);
+    int dmax = 0;
+    int rc = dedisperse_delays(n_chan, chan_freq_hz, dm, d.data(), &dmax);
+    if (rc) return rc;
+    *n_out = std::max<int64_t>(0, n_frames - dmax);
+    if (*n_out == 0) return BF_OK;
+    if (!d_out || !d_series) return fail(BF_EINVAL, "null buffer");
+    CK(cudaSetDevice(p->device));
+    int* table = nullptr;
+    CK(dedisperse_static_table(p->device, &table));
+    CK(cudaMemcpyAsync(table, d.data(), (size_t)n_sub * sizeof(int), cudaMemcpyHostToDevice, p->stream));
+    CK(dedisperse_launch(d_out, table, n_sub, (long long)n_frames, (long long)*n_out, d_series, p->stream));
+    return BF_OK;
+}
+
 
 int bf_rescale_u8(bf_plan_t p, const float* d_out, int64_t n_rows, int64_t n_frames, uint8_t* d_codes,
                   float* d_stats) {
