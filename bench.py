@@ -438,8 +438,13 @@ def main():
         form_outs[fname] = fo[:, :, :16].cpu().numpy()
 
     # end to end through the public API: pinned host in -> device -> beamform -> host out.
-    # One request per channel; the copy of channel c+1 overlaps the beamforming of c.
+    # One request per channel; the copy of channel c+1 overlaps the beamforming of c, and
+    # channels alternate between two plans on two streams so that the CTAs of the next
+    # channel fill the SMs a channel's last wave leaves idle (512 work items = 3.4 waves).
     copy_s, d2h_s = torch.cuda.Stream(), torch.cuda.Stream()
+    stream2 = torch.cuda.Stream()
+    plan2 = B.Plan(stream=stream2, form=headline_form)
+    e2e_plans = [(plan, stream), (plan2, stream2)]
     outs_c = [torch.empty(1024, 16, nf, dtype=torch.float32, device="cuda") for _ in range(N_CHAN)]
     host_outs = [torch.empty(1024, 16, nf, dtype=torch.float32).pin_memory() for _ in range(N_CHAN)]
     in_ev = [torch.cuda.Event() for _ in range(N_CHAN)]
@@ -452,16 +457,17 @@ def main():
                 in_ev[c].record(copy_s)
         tk = []
         for c in range(N_CHAN):                         # beamform channel c once it has landed
-            stream.wait_event(in_ev[c])
-            _, t = plan.submit(vin[c:c + 1], freqs[c:c + 1], outs_c[c], stream_id=100 + c,
-                               flags=B.BF_END_OF_STREAM)
-            done_ev[c].record(stream)
-            tk.append(t)
+            pl, st = e2e_plans[c % 2]
+            st.wait_event(in_ev[c])
+            _, t = pl.submit(vin[c:c + 1], freqs[c:c + 1], outs_c[c], stream_id=100 + c,
+                             flags=B.BF_END_OF_STREAM)
+            done_ev[c].record(st)
+            tk.append((pl, t))
             with torch.cuda.stream(d2h_s):              # device->host of each output as it is done
                 d2h_s.wait_event(done_ev[c])
                 host_outs[c].copy_(outs_c[c], non_blocking=True)
-        for t in tk:
-            plan.poll(t)
+        for pl, t in tk:
+            pl.poll(t)
         d2h_s.synchronize()
 
     e2e_step()
@@ -513,7 +519,8 @@ def main():
             "e2e": {"value": samples * ws / (e2e_ms * 1e-3), "unit": "input-samples/s",
                     "h2d_bytes_per_step": samples, "d2h_bytes_per_step": out.numel() * 4,
                     "ms_per_step": e2e_ms, "how": "wall clock; per-channel requests, H2D of channel c+1 "
-                                                  "overlapping beamforming of channel c, D2H of each output"},
+                                                  "overlapping beamforming of channel c, channels alternating "
+                                                  "between two plans on two streams, D2H of each output"},
             "gpu_launches": args.steps,
             "forms": form_runs,
             "post": post,
@@ -532,6 +539,7 @@ def main():
             line["cpu_baseline"] = cpu_baseline(raw, freqs, host_out.numpy(), form_outs)
             line["cpu_baseline"]["one_core"] = oracle_one_core(raw, freqs)
         print(json.dumps(line), flush=True)
+    plan2.close()
     plan.close()
     if ws > 1:
         dist.destroy_process_group()
