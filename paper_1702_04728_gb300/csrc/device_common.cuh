@@ -224,6 +224,37 @@ __device__ __forceinline__ void tmem_ld64(uint32_t taddr, cp (&y)[16]) {
 
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
+// ---------------------------------------------------------------------------
+// mbarriers with bounded waits
+// ---------------------------------------------------------------------------
+constexpr unsigned long long kWaitNs = 2000000000ull;   // default bound on every mbarrier wait (2 s)
+
+__device__ __forceinline__ unsigned long long globaltimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for the completion of phase `parity` of an mbarrier: false once `limit`
+// ns have passed without it.
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, unsigned long long limit) {
+    const unsigned long long t0 = globaltimer();
+    for (;;) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok) : "r"(mbar), "r"(parity) : "memory");
+        if (ok) return true;
+        if (globaltimer() - t0 > limit) return false;
+    }
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(mbar) : "memory");
+}
+
 // CTA barrier that also orders tensor-memory accesses across it.
 __device__ __forceinline__ void cta_sync() {
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");

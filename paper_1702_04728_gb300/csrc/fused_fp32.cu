@@ -35,20 +35,28 @@
 namespace chimebf {
 namespace {
 
-constexpr int kThreads = 256;
-constexpr int kWarps = kThreads / 32;       // 8: warp w loads row pair a = w
+constexpr int kWarps = 8;                   // phase-A (producer) warps: warp w loads row pair a = w
 constexpr int kPairs = kWarps / 2;
+constexpr int kCons = 4;                    // gather / up-channel (consumer) warps, one per TMEM lane quarter
+constexpr int kThreads = 32 * (kWarps + kCons);
+
+// named barriers: 0 = whole CTA; FULL of bin buffer b; one per warp pair; consumers only.
+// The release of a bin buffer (EMPTY) is an mbarrier the consumer warps arrive on, so
+// producer pairs wait for the consumers without waiting for each other.
+constexpr int kBarFull = 1, kBarPair = 5, kBarCons = 9;
 
 // shared memory (float4 = one SoA pair: re0, re1, im0, im1)
 constexpr int kBinsF4 = kWarps * kBins;             // 8 row pairs x 512 bins (one of two buffers)
 constexpr int kYscF4 = 2 * kFeed;                    // per warp pair: 2 row pairs x 256 feeds
-constexpr int kTbF4 = 2 * kFeed;                     // per warp: 2 row pairs x 16 x 16
+constexpr int kTbF4 = 2 * kFeed;                     // per warp: 2 row pairs x 16 x 16 (inside its pair's bins)
+constexpr int kRawB = 2 * kInput;                    // per producer warp and buffer: its two raw rows
 constexpr size_t kSmemBins = 2 * (size_t)kBinsF4 * 16;   // double-buffered across iterations
 constexpr size_t kSmemYsc = (size_t)kPairs * kYscF4 * 16;
-constexpr size_t kSmemTb = (size_t)kWarps * kTbF4 * 16;
+constexpr size_t kSmemRaw = 2 * (size_t)kWarps * kRawB;  // double-buffered raw rows (cp.async)
 constexpr size_t kSmemLut = kNs * sizeof(int);
 constexpr size_t kSmemTw = 8 * 8 * 16;               // pair twiddles of the first up-channel pass
-constexpr size_t kSmemTotal = kSmemBins + kSmemYsc + kSmemTb + kSmemLut + kSmemTw;
+constexpr size_t kSmemTotal = kSmemBins + kSmemYsc + kSmemRaw + kSmemLut + kSmemTw;
+static_assert(kTbF4 * 2 == 2 * kBins, "the pair's two transpose scratches fill its two bin rows");
 
 // ---------------------------------------------------------------------------
 // Phase A for one warp of a warp pair.
@@ -77,9 +85,10 @@ __device__ __forceinline__ cp lds_cp(uint32_t addr) {
     return a;
 }
 
+template <class BeforeTb>
 __device__ __forceinline__ void phase_a(const uint4 (&in0)[kCyl], const uint4 (&in1)[kCyl], uint32_t sel,
                                         const EwW& w, const PostTw& pt, uint32_t ysc, uint32_t tb, uint32_t bins2,
-                                        int e, int lane, int bar_id) {
+                                        int e, int lane, int bar_id, BeforeTb before_tb) {
     // unpack + E-W: lane holds feeds 8 lane .. 8 lane + 7 of both rows.  Feed n = 8 lane + 2k (+1)
     // sits at n2 = n & 15 = 8 (lane & 1) + 2k (+1), n1 = n >> 4 = lane >> 1; ysw(n2, n1) =
     // 16 n2 + (n1 ^ (n2 & 7) ^ 4 (n2 >> 3)) = 16 n2 + (((lane >> 1) ^ 4 (lane & 1)) ^ (n2 & 7)).
@@ -125,6 +134,8 @@ __device__ __forceinline__ void phase_a(const uint4 (&in0)[kCyl], const uint4 (&
     dft16(v);
 #pragma unroll
     for (int k1 = 0; k1 < 16; ++k1) v[k1] = cmulp(v[k1], pt.C[k1], pt.S[k1]);
+    // the transpose scratch may share memory with bins still being read elsewhere
+    before_tb();
     // transpose through tb: tsw(r, c) = 16 r + (c ^ (r & 7))
     const uint32_t tbl = tb + 16u * (uint32_t)(rp * kFeed);
     {
@@ -140,6 +151,9 @@ __device__ __forceinline__ void phase_a(const uint4 (&in0)[kCyl], const uint4 (&
         for (int r = 0; r < 16; ++r) v[r] = lds_cp((tr_ ^ (uint32_t)(16 * (r & 7))) + 256u * r);
     }
     dft16(v);
+    // both warps of the pair are done with their scratch before the bins (which may
+    // share its memory) are written
+    pair_sync(bar_id);
     // bin of the 512-point padded FFT: L = 2 (k1 + 16 k2) + e = 32 k2 + (2 k1 + e), and
     // bsw(L) = 32 k2 + bsw(2 k1 + e) because bit 3 of L does not depend on k2
     const uint32_t row = bins2 + 16u * (uint32_t)(rp * kBins + bsw(2 * k1 + e));
@@ -150,26 +164,50 @@ __device__ __forceinline__ void phase_a(const uint4 (&in0)[kCyl], const uint4 (&
 // ---------------------------------------------------------------------------
 // the fused kernel
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ void bar_sync_n(int id, int n) { asm volatile("bar.sync %0, %1;" :: "r"(id), "r"(n) : "memory"); }
+__device__ __forceinline__ void bar_arrive_n(int id, int n) { asm volatile("bar.arrive %0, %1;" :: "r"(id), "r"(n) : "memory"); }
+
+// 16-byte asynchronous global -> shared copy (no registers), grouped per iteration
+__device__ __forceinline__ void cp16(uint32_t dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" :: "r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" :: "n"(N) : "memory"); }
+
+__device__ __forceinline__ uint4 lds_u4(uint32_t addr) {
+    uint4 v;
+    asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(addr)
+                 : "memory");
+    return v;
+}
+
+// Warps 0-7 (producers) run phase A for their row pairs; warps 8-11 (consumers,
+// one per TMEM lane quarter) gather the clamped bins, run the first up-channel
+// pass into TMEM and, after each block, the second pass and the detection for
+// two bins each (m and m + 128).  The bin rows are double-buffered: producers
+// arrive on the named barrier FULL[b] after writing buffer b, consumers arrive on
+// the mbarrier EMPTY[b] after reading it, so phase A of iteration g + 1 overlaps
+// the gather of iteration g and the second up-channel pass.  A producer can only
+// be two iterations ahead of the slowest consumer and one FULL phase behind
+// the others, so no barrier phase ever mixes iterations.  The EMPTY waits are
+// bounded; on expiry the kernel carries on (keeping every barrier matched) and
+// reports through the status word.
 template <bool kDump>
 __global__ void __launch_bounds__(kThreads, 1) fused_fp32_kernel(const __grid_constant__ Batch bt) {
     extern __shared__ __align__(256) unsigned char smem[];   // the swizzles XOR address bits 4-7
     float4* bins_all = reinterpret_cast<float4*>(smem);
     float4* ysc_all = reinterpret_cast<float4*>(smem + kSmemBins);
-    float4* tb_all = reinterpret_cast<float4*>(smem + kSmemBins + kSmemYsc);
-    int* lut_s = reinterpret_cast<int*>(smem + kSmemBins + kSmemYsc + kSmemTb);
-    float4* tw_s = reinterpret_cast<float4*>(smem + kSmemBins + kSmemYsc + kSmemTb + kSmemLut);
+    unsigned char* raw_all = smem + kSmemBins + kSmemYsc;
+    int* lut_s = reinterpret_cast<int*>(smem + kSmemBins + kSmemYsc + kSmemRaw);
+    float4* tw_s = reinterpret_cast<float4*>(smem + kSmemBins + kSmemYsc + kSmemRaw + kSmemLut);
     __shared__ uint32_t tmem_base_s;
+    __shared__ __align__(8) uint64_t empty_s[2];
+    __shared__ int expired_s;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int e = warp & 1, q = warp >> 1;
-    const uint32_t ysc_sa = smem_sa(ysc_all + q * kYscF4);
-    const uint32_t tb_sa = smem_sa(tb_all + warp * kTbF4);
-
-
-    // gather / second pass role: TMEM lane quarter = warp & 3, bin half = warp >> 2
-    const int ell = 32 * (warp & 3) + lane;
-    const int hh = warp >> 2;
-    const int m = ell + 128 * hh;
+    constexpr int kAll = kThreads;
+    const uint32_t empty0 = smem_sa(&empty_s[0]);
 
     if (warp == 0) {
         const uint32_t dst = static_cast<uint32_t>(__cvta_generic_to_shared(&tmem_base_s));
@@ -183,96 +221,154 @@ __global__ void __launch_bounds__(kThreads, 1) fused_fp32_kernel(const __grid_co
         const float2 w1 = bt.tw128[((2 * it + 1) * c) & (kUp - 1)];
         tw_s[i] = make_float4(w0.x, w1.x, w0.y, w1.y);
     }
+    if (tid == 0) {
+        for (int i = 0; i < 2; ++i)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(empty0 + 8u * i), "n"(kCons) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        expired_s = 0;
+    }
     cta_sync();
     const uint32_t tmem = tmem_base_s;
-    const uint32_t tlane = tmem + (static_cast<uint32_t>(32 * (warp & 3)) << 16);
+    constexpr int kPasses = kTds * kPol;
+    const unsigned long long wlim = bt.wait_ns ? bt.wait_ns : kWaitNs;
 
-    PostTw pt;
-    load_post(bt.tw512, lane & 15, e, pt);
-
-    int par = 0;                     // bins buffer of the next iteration
-    for (int item = blockIdx.x; item < bt.n_items; item += gridDim.x) {
-        int sgi = 0;
-        while (sgi + 1 < bt.n_segs && bt.segs[sgi + 1].item_begin <= item) ++sgi;
-        const Seg& sg = bt.segs[sgi];
-        const int local = item - sg.item_begin;
-        const int F = local >> 2, j = local & 3;
-
-        for (int i = tid; i < kNs; i += kThreads) lut_s[i] = bt.lut[sg.table * kNs + i];
-        EwW w;
-        load_ew_frame(sg, bt.ew, F, j, w);
-        cta_sync();
-        const int Lsw = bsw(lut_s[m]);
-
-        float2 acc[kSub];
+    if (warp < kWarps) {
+        // ---------------------------------- producers ----------------------------------
+        const int e = warp & 1, q = warp >> 1;
+        const uint32_t ysc_sa = smem_sa(ysc_all + q * kYscF4);
+        const uint32_t raw_sa = smem_sa(raw_all) + (uint32_t)(warp * kRawB) + 16u * lane;
+        PostTw pt;
+        load_post(bt.tw512, lane & 15, e, pt);
+        uint32_t g = 0;                                   // iterations done by this CTA
+        for (int item = blockIdx.x; item < bt.n_items; item += gridDim.x) {
+            int sgi = 0;
+            while (sgi + 1 < bt.n_segs && bt.segs[sgi + 1].item_begin <= item) ++sgi;
+            const Seg& sg = bt.segs[sgi];
+            const int local = item - sg.item_begin;
+            const int F = local >> 2, j = local & 3;
+            EwW w;
+            load_ew_frame(sg, bt.ew, F, j, w);
+            const long long row0 = (long long)F * kFrame + 16 * warp;
+            // this warp's two rows of iteration (ps, it) into raw buffer rb (own bytes only)
+            auto fetch = [&](int ps, int it, uint32_t rb) {
+                const long long r = row0 + (ps >> 1) * kUp + 2 * it;
+                const uint8_t* p0 = frame_row(sg, r) + 16 * lane;
+                const uint8_t* p1 = frame_row(sg, r + 1) + 16 * lane;
+                const uint32_t d = raw_sa + rb * (uint32_t)(kWarps * kRawB);
 #pragma unroll
-        for (int s = 0; s < kSub; ++s) acc[s] = make_float2(0.f, 0.f);
-
-        const long long row0 = (long long)F * kFrame;
-        // raw rows of the current iteration and the prefetched next one; the loop body is
-        // unrolled twice with the roles swapped so the rows are never copied
-        uint4 ra0[kCyl], ra1[kCyl], rb0[kCyl], rb1[kCyl];
-        load_row(frame_row(sg, row0 + 16 * warp), lane, ra0);
-        load_row(frame_row(sg, row0 + 16 * warp + 1), lane, ra1);
-
-        for (int ps = 0; ps < kTds * kPol; ++ps) {
-            const int blk = ps >> 1, pol = ps & 1;
-            const uint32_t sel = 0x4400u | ((2u + pol) << 4) | (uint32_t)pol;
-            auto step = [&](int it, const uint4 (&cur0)[kCyl], const uint4 (&cur1)[kCyl], uint4 (&nxt0)[kCyl],
-                            uint4 (&nxt1)[kCyl]) {
-                const bool more = it < 7 || ps + 1 < kTds * kPol;
-                if (more) {
-                    const int nit = it < 7 ? it + 1 : 0;
-                    const int nblk = it < 7 ? blk : ((ps + 1) >> 1);
-                    const long long r = row0 + nblk * kUp + 16 * warp + 2 * nit;
-                    load_row(frame_row(sg, r), lane, nxt0);
-                    load_row(frame_row(sg, r + 1), lane, nxt1);
+                for (int c = 0; c < kCyl; ++c) {
+                    cp16(d + c * (kFeed * kPol), p0 + c * (kFeed * kPol));
+                    cp16(d + kInput + c * (kFeed * kPol), p1 + c * (kFeed * kPol));
                 }
-                // bins of this iteration: one buffer while the other is still being gathered
-                float4* bins = bins_all + par * kBinsF4;
-                par ^= 1;
-                phase_a(cur0, cur1, sel, w, pt, ysc_sa, tb_sa, smem_sa(bins + (2 * q) * kBins), e, lane, 1 + q);
-                cta_sync();
-                // gather + 8-point DFT over a (tau = 16 a + b, b = 2 it, 2 it + 1)
-                cp z[8];
-#pragma unroll
-                for (int a = 0; a < 8; ++a) z[a] = ld_cp(bins + a * kBins + Lsw);
-                dft8(z);
-                const int b0 = 2 * it;
-#pragma unroll
-                for (int c = 0; c < 8; ++c) {
-                    if (c) {
-                        const float4 t = tw_s[it * 8 + c];
-                        z[c] = cmulp(z[c], make_float2(t.x, t.y), make_float2(t.z, t.w));
-                    }
-                    tmem_st4(tlane + hh * 256 + 2 * (16 * c + b0), z[c].re.x, z[c].im.x, z[c].re.y, z[c].im.y);
-                }
-                // no barrier here: the next iteration writes the other bins buffer, and the
-                // barrier after its phase A orders this gather before the buffer's reuse
+                cp_commit();
             };
+            fetch(0, 0, g & 1u);
+            for (int ps = 0; ps < kPasses; ++ps) {
+                const int pol = ps & 1;
+                const uint32_t sel = 0x4400u | ((2u + pol) << 4) | (uint32_t)pol;
 #pragma unroll 1
-            for (int it = 0; it < 8; it += 2) {
-                step(it, ra0, ra1, rb0, rb1);
-                step(it + 1, rb0, rb1, ra0, ra1);
-            }
-            tmem_wait_st();
-            cta_sync();
-            // second pass: 16-point DFT over b for fine channels q = c + 8 d
-            upchan_pass2(tlane, hh, acc,
-                         kDump ? bt.dump + ((((long long)(F * kTds + blk) * kPol + pol) * kEw + j) * kNs + m) * kUp
-                               : nullptr);
-            // the next pass's first gather overwrites TMEM after two CTA barriers
-        }
-
-        if constexpr (!kDump) {
-            float* o = sg.out + (long long)(kNs * j + m) * sg.beam_stride + F;
+                for (int it = 0; it < 8; ++it, ++g) {
+                    const uint32_t b = g & 1u;
+                    // rows of the next iteration of this item, then this iteration's rows
+                    if (it < 7 || ps + 1 < kPasses) {
+                        fetch(it < 7 ? ps : ps + 1, it < 7 ? it + 1 : 0, b ^ 1u);
+                        cp_wait<1>();
+                    } else {
+                        cp_wait<0>();
+                    }
+                    const uint32_t rs = raw_sa + b * (uint32_t)(kWarps * kRawB);
+                    uint4 in0[kCyl], in1[kCyl];
 #pragma unroll
-            for (int s = 0; s < kSub; ++s) o[(long long)s * sg.sub_stride] = acc[s].x + acc[s].y;
+                    for (int c = 0; c < kCyl; ++c) {
+                        in0[c] = lds_u4(rs + c * (kFeed * kPol));
+                        in1[c] = lds_u4(rs + kInput + c * (kFeed * kPol));
+                    }
+                    const uint32_t pair_bins = smem_sa(bins_all + b * kBinsF4 + (2 * q) * kBins);
+                    phase_a(in0, in1, sel, w, pt, ysc_sa, pair_bins + (uint32_t)(e * kTbF4 * 16), pair_bins, e,
+                            lane, kBarPair + q, [&] {
+                                // buffer b is free once the consumers gathered it two iterations ago
+                                // (release number g / 2 - 1 of buffer b)
+                                if (g >= 2 && !mbar_wait(empty0 + 8u * b, ((g >> 1) + 1u) & 1u, wlim))
+                                    expired_s = 1;
+                            });
+                    bar_arrive_n(kBarFull + (int)b, kAll);
+                }
+            }
         }
-        cta_sync();
+    } else {
+        // ---------------------------------- consumers ----------------------------------
+        const int cq = warp - kWarps;                    // TMEM lane quarter
+        const int ctid = tid - 32 * kWarps;
+        const uint32_t tlane = tmem + (static_cast<uint32_t>(32 * cq) << 16);
+        const int m0 = 32 * cq + lane;                   // bins m0 (half 0) and m0 + 128 (half 1)
+        uint32_t g = 0;
+        for (int item = blockIdx.x; item < bt.n_items; item += gridDim.x) {
+            int sgi = 0;
+            while (sgi + 1 < bt.n_segs && bt.segs[sgi + 1].item_begin <= item) ++sgi;
+            const Seg& sg = bt.segs[sgi];
+            const int local = item - sg.item_begin;
+            const int F = local >> 2, j = local & 3;
+            bar_sync_n(kBarCons, 32 * kCons);             // the previous item's table reads are done
+            for (int i = ctid; i < kNs; i += 32 * kCons) lut_s[i] = bt.lut[sg.table * kNs + i];
+            bar_sync_n(kBarCons, 32 * kCons);
+            const int Lsw0 = bsw(lut_s[m0]), Lsw1 = bsw(lut_s[m0 + 128]);
+            float2 acc0[kSub], acc1[kSub];
+#pragma unroll
+            for (int s2 = 0; s2 < kSub; ++s2) {
+                acc0[s2] = make_float2(0.f, 0.f);
+                acc1[s2] = make_float2(0.f, 0.f);
+            }
+            for (int ps = 0; ps < kPasses; ++ps) {
+                const int blk = ps >> 1, pol = ps & 1;
+#pragma unroll 1
+                for (int it = 0; it < 8; ++it, ++g) {
+                    const uint32_t b = g & 1u;
+                    bar_sync_n(kBarFull + (int)b, kAll);
+                    const float4* bins = bins_all + b * kBinsF4;
+                    // gather + 8-point DFT over a (tau = 16 a + b, b = 2 it, 2 it + 1), both bin halves
+#pragma unroll
+                    for (int hh = 0; hh < 2; ++hh) {
+                        const int Lsw = hh ? Lsw1 : Lsw0;
+                        cp z[8];
+#pragma unroll
+                        for (int a = 0; a < 8; ++a) z[a] = ld_cp(bins + a * kBins + Lsw);
+                        dft8(z);
+                        const int b0 = 2 * it;
+#pragma unroll
+                        for (int c = 0; c < 8; ++c) {
+                            if (c) {
+                                const float4 t = tw_s[it * 8 + c];
+                                z[c] = cmulp(z[c], make_float2(t.x, t.y), make_float2(t.z, t.w));
+                            }
+                            tmem_st4(tlane + hh * 256 + 2 * (16 * c + b0), z[c].re.x, z[c].im.x, z[c].re.y,
+                                     z[c].im.y);
+                        }
+                    }
+                    __syncwarp();                                   // this warp's reads of buffer b are done
+                    if (lane == 0) mbar_arrive(empty0 + 8u * b);
+                }
+                tmem_wait_st();
+                // second pass: 16-point DFT over b for fine channels q = c + 8 d (this warp's lanes only)
+                const long long dbase = ((((long long)(F * kTds + blk) * kPol + pol) * kEw + j) * kNs) * kUp;
+                upchan_pass2(tlane, 0, acc0, kDump ? bt.dump + dbase + (long long)m0 * kUp : nullptr);
+                upchan_pass2(tlane, 1, acc1, kDump ? bt.dump + dbase + (long long)(m0 + 128) * kUp : nullptr);
+                // the next pass's gathers overwrite these TMEM columns in this warp's program order
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            }
+            if constexpr (!kDump) {
+                float* o0 = sg.out + (long long)(kNs * j + m0) * sg.beam_stride + F;
+                float* o1 = sg.out + (long long)(kNs * j + m0 + 128) * sg.beam_stride + F;
+#pragma unroll
+                for (int s2 = 0; s2 < kSub; ++s2) {
+                    o0[(long long)s2 * sg.sub_stride] = acc0[s2].x + acc0[s2].y;
+                    o1[(long long)s2 * sg.sub_stride] = acc1[s2].x + acc1[s2].y;
+                }
+            }
+        }
     }
 
     cta_sync();
+    if (expired_s && tid == 0 && bt.status) atomicExch(bt.status, 1);
     if (warp == 0) {
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" :: "r"(tmem) : "memory");
     }
@@ -302,7 +398,7 @@ __global__ void __launch_bounds__(64) debug_beams_kernel(const uint8_t* __restri
     load_row(vin + ra * kInput, lane, in0);
     load_row(vin + rb * kInput, lane, in1);
     const uint32_t sel = 0x4400u | ((2u + pol) << 4) | (uint32_t)pol;
-    phase_a(in0, in1, sel, w, pt, smem_sa(ysc), smem_sa(tbs[warp]), smem_sa(bins2), e, lane, 1);
+    phase_a(in0, in1, sel, w, pt, smem_sa(ysc), smem_sa(tbs[warp]), smem_sa(bins2), e, lane, 1, [] {});
     __syncthreads();
     for (int i = threadIdx.x; i < 4 * kNs; i += 64) {
         const int r = i >> 8, mm = i & 255;          // r: row 0..3 = slot (r >> 1), element (r & 1)

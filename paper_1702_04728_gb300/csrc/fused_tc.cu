@@ -37,7 +37,6 @@
 namespace chimebf {
 namespace {
 
-constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s bound on every mbarrier wait
 
 template <int TERMS>
 struct TcCfg {
@@ -84,28 +83,6 @@ __device__ __forceinline__ void mma_f16(uint32_t dtmem, uint64_t adesc, uint64_t
 __device__ __forceinline__ void mma_commit(uint32_t mbar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" :: "r"(mbar)
                  : "memory");
-}
-
-__device__ __forceinline__ unsigned long long globaltimer() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-// Bounded wait for the completion of phase `parity` of an mbarrier: false once
-// `limit` ns have passed without it.
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, unsigned long long limit) {
-    const unsigned long long t0 = globaltimer();
-    for (;;) {
-        uint32_t ok;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}"
-            : "=r"(ok) : "r"(mbar), "r"(parity) : "memory");
-        if (ok) return true;
-        if (globaltimer() - t0 > limit) return false;
-    }
 }
 
 // TMEM access for the split Re/Im layout: 16 two-column loads (Re at base +
@@ -323,9 +300,6 @@ __device__ __forceinline__ void mbar_expect(uint32_t mbar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(mbar), "r"(bytes) : "memory");
 }
 
-__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(mbar) : "memory");
-}
 
 // MODE: 0 = detect and integrate, 1 = dump up-channelised voltages,
 //       2 = dump the N-S/E-W beams of the GEMM (stage dump), 3 = stall check
