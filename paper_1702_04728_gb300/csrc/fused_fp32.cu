@@ -36,27 +36,26 @@ namespace chimebf {
 namespace {
 
 constexpr int kWarps = 8;                   // phase-A (producer) warps: warp w loads row pair a = w
-constexpr int kPairs = kWarps / 2;
 constexpr int kCons = 4;                    // gather / up-channel (consumer) warps, one per TMEM lane quarter
 constexpr int kThreads = 32 * (kWarps + kCons);
 
-// named barriers: 0 = whole CTA; FULL of bin buffer b; one per warp pair; consumers only.
-// The release of a bin buffer (EMPTY) is an mbarrier the consumer warps arrive on, so
-// producer pairs wait for the consumers without waiting for each other.
-constexpr int kBarFull = 1, kBarPair = 5, kBarCons = 9;
+// named barriers: 0 = whole CTA; FULL of bin buffer b; consumers only.  The release of a
+// bin buffer (EMPTY) is an mbarrier the consumer warps arrive on, so producer warps wait
+// for the consumers without waiting for each other.
+constexpr int kBarFull = 1, kBarCons = 3;
 
 // shared memory (float4 = one SoA pair: re0, re1, im0, im1)
 constexpr int kBinsF4 = kWarps * kBins;             // 8 row pairs x 512 bins (one of two buffers)
-constexpr int kYscF4 = 2 * kFeed;                    // per warp pair: 2 row pairs x 256 feeds
-constexpr int kTbF4 = 2 * kFeed;                     // per warp: 2 row pairs x 16 x 16 (inside its pair's bins)
+constexpr int kYscF4 = kFeed;                        // per warp: its row pair's 256 phased feed lines
+constexpr int kTbF4 = 2 * kFeed;                     // per warp: 2 halves x 16 x 16 (inside its own bin row)
 constexpr int kRawB = 2 * kInput;                    // per producer warp and buffer: its two raw rows
 constexpr size_t kSmemBins = 2 * (size_t)kBinsF4 * 16;   // double-buffered across iterations
-constexpr size_t kSmemYsc = (size_t)kPairs * kYscF4 * 16;
+constexpr size_t kSmemYsc = (size_t)kWarps * kYscF4 * 16;
 constexpr size_t kSmemRaw = 2 * (size_t)kWarps * kRawB;  // double-buffered raw rows (cp.async)
 constexpr size_t kSmemLut = kNs * sizeof(int);
 constexpr size_t kSmemTw = 8 * 8 * 16;               // pair twiddles of the first up-channel pass
 constexpr size_t kSmemTotal = kSmemBins + kSmemYsc + kSmemRaw + kSmemLut + kSmemTw;
-static_assert(kTbF4 * 2 == 2 * kBins, "the pair's two transpose scratches fill its two bin rows");
+static_assert(kTbF4 == kBins, "a warp's transpose scratch is exactly its bin row");
 
 // ---------------------------------------------------------------------------
 // Phase A for one warp of a warp pair.
@@ -85,14 +84,24 @@ __device__ __forceinline__ cp lds_cp(uint32_t addr) {
     return a;
 }
 
+// Phase A for one warp and its row pair (two time rows as SoA pairs):
+//   in0/in1   the two raw rows
+//   sel       byte permutation selecting polarisation pol of two feeds
+//   ysc       this warp's phased feed lines [16 n2][16 n1] (swizzled, 4 KB)
+//   tb        this warp's transpose scratch [2 halves][16][16] (8 KB; may be the bin row)
+//   row_bins  the row pair's 512 bins (8 KB)
+// Lanes 0-15 compute the even bins (FFT256 of y), lanes 16-31 the odd bins
+// (FFT256 of y exp(-i pi n / 256)) of the zero-padded 512-point N-S FFT, lane
+// n2 = lane & 15 in each half; `pt` holds that lane's twiddles.  Only warp-level
+// synchronisation: no other warp touches this warp's scratch.
 template <class BeforeTb>
 __device__ __forceinline__ void phase_a(const uint4 (&in0)[kCyl], const uint4 (&in1)[kCyl], uint32_t sel,
-                                        const EwW& w, const PostTw& pt, uint32_t ysc, uint32_t tb, uint32_t bins2,
-                                        int e, int lane, int bar_id, BeforeTb before_tb) {
+                                        const EwW& w, const PostTw& pt, uint32_t ysc, uint32_t tb, uint32_t row_bins,
+                                        int lane, BeforeTb before_tb) {
     // unpack + E-W: lane holds feeds 8 lane .. 8 lane + 7 of both rows.  Feed n = 8 lane + 2k (+1)
     // sits at n2 = n & 15 = 8 (lane & 1) + 2k (+1), n1 = n >> 4 = lane >> 1; ysw(n2, n1) =
     // 16 n2 + (n1 ^ (n2 & 7) ^ 4 (n2 >> 3)) = 16 n2 + (((lane >> 1) ^ 4 (lane & 1)) ^ (n2 & 7)).
-    const uint32_t yw = ysc + 16u * (uint32_t)(e * kFeed + 16 * 8 * (lane & 1) + (((lane >> 1) ^ (4 * (lane & 1)))));
+    const uint32_t yw = ysc + 16u * (uint32_t)(16 * 8 * (lane & 1) + (((lane >> 1) ^ (4 * (lane & 1)))));
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         cp yA, yB;
@@ -116,16 +125,16 @@ __device__ __forceinline__ void phase_a(const uint4 (&in0)[kCyl], const uint4 (&
         sts_cp((yw ^ (uint32_t)(16 * (2 * k))) + 256u * (2 * k), yA);
         sts_cp((yw ^ (uint32_t)(16 * (2 * k + 1))) + 256u * (2 * k + 1), yB);
     }
-    pair_sync(bar_id);
+    __syncwarp();
 
-    // lanes 0-15: row pair slot 0, lanes 16-31: slot 1; lane handles n2:
+    // half h = lane >> 4 of the padded FFT, lane handles n2 (both halves read the same lines):
     // ysw(n2, n1) = 16 n2 + (n1 ^ f), f = (n2 & 7) ^ 4 (n2 >> 3)
-    const int rp = lane >> 4, n2 = lane & 15;
-    const uint32_t yr = ysc + 16u * (uint32_t)(rp * kFeed + 16 * n2 + ((n2 & 7) ^ (4 * (n2 >> 3))));
+    const int h = lane >> 4, n2 = lane & 15;
+    const uint32_t yr = ysc + 16u * (uint32_t)(16 * n2 + ((n2 & 7) ^ (4 * (n2 >> 3))));
     cp v[16];
 #pragma unroll
     for (int n1 = 0; n1 < 16; ++n1) v[n1] = lds_cp(yr ^ (uint32_t)(16 * n1));
-    if (e) {
+    if (h) {
         // odd bins: input times exp(-i pi n / 256) = exp(-2 pi i n1 / 32) * exp(-2 pi i n2 / 512);
         // the second factor is folded into the per-lane twiddles
 #pragma unroll
@@ -136,8 +145,8 @@ __device__ __forceinline__ void phase_a(const uint4 (&in0)[kCyl], const uint4 (&
     for (int k1 = 0; k1 < 16; ++k1) v[k1] = cmulp(v[k1], pt.C[k1], pt.S[k1]);
     // the transpose scratch may share memory with bins still being read elsewhere
     before_tb();
-    // transpose through tb: tsw(r, c) = 16 r + (c ^ (r & 7))
-    const uint32_t tbl = tb + 16u * (uint32_t)(rp * kFeed);
+    // transpose through tb (one 4 KB block per half): tsw(r, c) = 16 r + (c ^ (r & 7))
+    const uint32_t tbl = tb + 16u * (uint32_t)(h * kFeed);
     {
         const uint32_t tw_ = tbl + 256u * (uint32_t)n2 + 16u * (uint32_t)(n2 & 7);
 #pragma unroll
@@ -151,12 +160,11 @@ __device__ __forceinline__ void phase_a(const uint4 (&in0)[kCyl], const uint4 (&
         for (int r = 0; r < 16; ++r) v[r] = lds_cp((tr_ ^ (uint32_t)(16 * (r & 7))) + 256u * r);
     }
     dft16(v);
-    // both warps of the pair are done with their scratch before the bins (which may
-    // share its memory) are written
-    pair_sync(bar_id);
-    // bin of the 512-point padded FFT: L = 2 (k1 + 16 k2) + e = 32 k2 + (2 k1 + e), and
-    // bsw(L) = 32 k2 + bsw(2 k1 + e) because bit 3 of L does not depend on k2
-    const uint32_t row = bins2 + 16u * (uint32_t)(rp * kBins + bsw(2 * k1 + e));
+    // every lane is done with the scratch before the bins (which may share its memory) are written
+    __syncwarp();
+    // bin of the 512-point padded FFT: L = 2 (k1 + 16 k2) + h = 32 k2 + (2 k1 + h), and
+    // bsw(L) = 32 k2 + bsw(2 k1 + h) because bit 3 of L does not depend on k2
+    const uint32_t row = row_bins + 16u * (uint32_t)bsw(2 * k1 + h);
 #pragma unroll
     for (int k2 = 0; k2 < 16; ++k2) sts_cp(row + 16u * 32u * k2, v[k2]);
 }
@@ -234,11 +242,10 @@ __global__ void __launch_bounds__(kThreads, 1) fused_fp32_kernel(const __grid_co
 
     if (warp < kWarps) {
         // ---------------------------------- producers ----------------------------------
-        const int e = warp & 1, q = warp >> 1;
-        const uint32_t ysc_sa = smem_sa(ysc_all + q * kYscF4);
+        const uint32_t ysc_sa = smem_sa(ysc_all + warp * kYscF4);
         const uint32_t raw_sa = smem_sa(raw_all) + (uint32_t)(warp * kRawB) + 16u * lane;
         PostTw pt;
-        load_post(bt.tw512, lane & 15, e, pt);
+        load_post(bt.tw512, lane & 15, lane >> 4, pt);
         uint32_t g = 0;                                   // iterations done by this CTA
         for (int item = blockIdx.x; item < bt.n_items; item += gridDim.x) {
             int sgi = 0;
@@ -283,9 +290,8 @@ __global__ void __launch_bounds__(kThreads, 1) fused_fp32_kernel(const __grid_co
                         in0[c] = lds_u4(rs + c * (kFeed * kPol));
                         in1[c] = lds_u4(rs + kInput + c * (kFeed * kPol));
                     }
-                    const uint32_t pair_bins = smem_sa(bins_all + b * kBinsF4 + (2 * q) * kBins);
-                    phase_a(in0, in1, sel, w, pt, ysc_sa, pair_bins + (uint32_t)(e * kTbF4 * 16), pair_bins, e,
-                            lane, kBarPair + q, [&] {
+                    const uint32_t row_bins = smem_sa(bins_all + b * kBinsF4 + warp * kBins);
+                    phase_a(in0, in1, sel, w, pt, ysc_sa, row_bins, row_bins, lane, [&] {
                                 // buffer b is free once the consumers gathered it two iterations ago
                                 // (release number g / 2 - 1 of buffer b)
                                 if (g >= 2 && !mbar_wait(empty0 + 8u * b, ((g >> 1) + 1u) & 1u, wlim))
@@ -383,14 +389,14 @@ __global__ void __launch_bounds__(64) debug_beams_kernel(const uint8_t* __restri
                                                           const int16_t* __restrict__ lut,
                                                           const float2* __restrict__ ew, const float2* __restrict__ tw512,
                                                           float2* __restrict__ out) {
-    __shared__ __align__(256) float4 ysc[kYscF4];         // 256-byte rows: the swizzles XOR address bits 4-7
+    __shared__ __align__(256) float4 ysc[2 * kYscF4];     // 256-byte rows: the swizzles XOR address bits 4-7
     __shared__ __align__(256) float4 tbs[2][kTbF4];
     __shared__ __align__(256) float4 bins2[2 * kBins];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, e = warp;
     const long long t0 = (long long)blockIdx.x * 4;
     const int pol = blockIdx.y & 1, j = blockIdx.y >> 1;
     PostTw pt;
-    load_post(tw512, lane & 15, e, pt);
+    load_post(tw512, lane & 15, lane >> 4, pt);
     EwW w;
     load_ew(ew, 0, j, w);
     uint4 in0[kCyl], in1[kCyl];
@@ -398,7 +404,8 @@ __global__ void __launch_bounds__(64) debug_beams_kernel(const uint8_t* __restri
     load_row(vin + ra * kInput, lane, in0);
     load_row(vin + rb * kInput, lane, in1);
     const uint32_t sel = 0x4400u | ((2u + pol) << 4) | (uint32_t)pol;
-    phase_a(in0, in1, sel, w, pt, smem_sa(ysc), smem_sa(tbs[warp]), smem_sa(bins2), e, lane, 1, [] {});
+    phase_a(in0, in1, sel, w, pt, smem_sa(ysc + e * kYscF4), smem_sa(tbs[warp]), smem_sa(bins2 + e * kBins), lane,
+            [] {});
     __syncthreads();
     for (int i = threadIdx.x; i < 4 * kNs; i += 64) {
         const int r = i >> 8, mm = i & 255;          // r: row 0..3 = slot (r >> 1), element (r & 1)
