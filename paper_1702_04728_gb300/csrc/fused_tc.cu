@@ -48,7 +48,8 @@ struct TcCfg {
     static constexpr bool B_LO = TERMS >= 2;
     static constexpr int A_STAGE = OPER * (A_LO ? 2 : 1);         // twiddle ring stage
     static constexpr int B_STAGE = OPER * (B_LO ? 2 : 1);         // data ring stage
-    static constexpr int NA = 3;                                  // twiddle ring depth
+    static constexpr int NA = 2;                                  // twiddle ring depth (a smaller shared-memory
+                                                                  // footprint leaves L1 for the raw loads)
     static constexpr int NOCT = KC / 16;                          // 8-feed octets per chunk
     static constexpr int NT = 288;                                // 8 producer warps + 1 MMA warp
     static constexpr int NPROD = 256;                             // producer threads
@@ -547,7 +548,7 @@ size_t tc_a_bytes(int terms) {
     return terms == 3 ? 2 * one : one;
 }
 
-int tc_chunk_k(int terms) { return terms == 3 ? TcCfg<3>::KC : TcCfg<1>::KC; }
+int tc_chunk_k(int terms) { return terms == 3 ? TcCfg<3>::KC : terms == 2 ? TcCfg<2>::KC : TcCfg<1>::KC; }
 
 cudaError_t fused_tc_launch(const Batch& b, int terms, int mode, int grid, cudaStream_t s) {
     switch (terms * 10 + mode) {

@@ -53,19 +53,23 @@ def run_stream(plan, st, out_list, lock=None, budget_wait=False):
     out_list.append((st["id"], torch.cat(outs, dim=2).cpu()))
 
 
-def test_mixed_batches_equal_alone(built_lib):
+@pytest.mark.parametrize("form", [B.BF_FP32_FFT, B.BF_TC_DFT256])
+def test_mixed_batches_equal_alone(built_lib, form):
+    """In the tensor-core form a mixed batch holds segments of many channel
+    frequencies, so the twiddle images change from chunk to chunk within one
+    launch; the results must still match the single-stream runs bit for bit."""
     streams = make_streams(10, seed=1)
     torch.cuda.synchronize()
     # alone: one stream at a time on a direct plan
     alone = {}
-    with B.Plan(mode=B.BF_MODE_DIRECT) as p:
+    with B.Plan(mode=B.BF_MODE_DIRECT, form=form) as p:
         for st in streams:
             res = []
             run_stream(p, st, res)
             alone[res[0][0]] = res[0][1]
     # mixed: all streams from 5 host threads on one serving plan
     mixed = []
-    with B.Plan(mode=B.BF_MODE_SERVING, stream=None) as p:
+    with B.Plan(mode=B.BF_MODE_SERVING, stream=None, form=form) as p:
         groups = [streams[i::5] for i in range(5)]
         ths = [threading.Thread(target=lambda g=g: [run_stream(p, st, mixed) for st in g]) for g in groups]
         for t in ths:
