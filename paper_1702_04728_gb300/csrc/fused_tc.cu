@@ -211,11 +211,17 @@ struct RawB {
     uint4 v[TASKS][kCyl];
 };
 
+// Lane bits 0-2 pick the time row within a group of 8, the next bits the
+// octet, the rest (with the warp and the task index) the group: one warp load
+// instruction then reads whole 32-byte sectors (all octets of 8 rows), and each
+// quarter warp stores 8 distinct 16-byte rows of a core matrix (no conflicts).
 template <int TERMS>
 __device__ __forceinline__ void task_of(int tid, int i, int& t, int& oct) {
     using C = TcCfg<TERMS>;
-    oct = (tid >> 5) % C::NOCT;
-    t = (tid & 31) + 32 * ((tid >> 5) / C::NOCT) + i * (C::NPROD / C::NOCT);
+    constexpr int RPW = 32 / C::NOCT;                 // time rows per warp and task (8 or 16)
+    const int lane = tid & 31, warp = tid >> 5;
+    oct = (lane >> 3) % C::NOCT;
+    t = (lane & 7) + 8 * (lane / (8 * C::NOCT)) + RPW * warp + i * (C::NPROD / C::NOCT);
 }
 
 template <int TERMS>
