@@ -167,6 +167,25 @@ def test_node_slice_full_size_sampled(plan):
     assert_rel(got, ref)
 
 
+@pytest.mark.parametrize("form", [B.BF_FP32_FFT, B.BF_TC_DFT256])
+def test_more_channels_than_one_launch_holds(built_lib, form):
+    """200 channels (segments) exceed one launch's 160 segment descriptors, so the
+    request runs as several launches; every channel's frames must still land in
+    their place.  Channel frequencies repeat, so table reuse is covered too."""
+    n_chan, T = 200, 384 * 2 + 17
+    freqs = [400e6 + 390625.0 * (7 * c % 1024 + 0.5) for c in range(n_chan)]
+    freqs[150:] = freqs[:50]                                   # repeated frequencies
+    raw = rand_raw((n_chan, T, 2048), seed=91, lo=-7)
+    rng = np.random.default_rng(92)
+    with B.Plan(form=form) as p:
+        out = p.run(dev(raw), freqs).cpu().numpy()
+    assert out.shape == (1024, 16 * n_chan, 2)
+    picks = [(ch, int(rng.integers(1024)), fr) for ch in (0, 1, 79, 159, 160, 161, 199) for fr in (0, 1)]
+    ref = O.beamform_sample(raw, freqs, picks)
+    got = np.stack([out[b, 16 * ch:16 * ch + 16, fr] for ch, b, fr in picks])
+    assert_rel(got, ref)                       # 1e-5: FP32 form and the 3-term tensor-core form
+
+
 def test_bad_arguments(plan):
     vin = torch.zeros(1, 384 * 2 + 1, 2048, dtype=torch.uint8, device="cuda")
     out = torch.empty(1024, 16, 2, dtype=torch.float32, device="cuda")
