@@ -24,6 +24,8 @@ constexpr int kBeams = kEw * kNs;    // 1024 intensity beams
 
 // Segments per launch (kernel-parameter space holds the descriptors).
 constexpr int kMaxSegs = 160;
+// Items of one launch that the FP32 kernel may split in two (at most half its grid).
+constexpr int kMaxSplit = 512;
 
 // One (request, channel): a frame stream made of `carry_rows` leftover rows
 // followed by the request's new rows.
@@ -53,6 +55,8 @@ struct Batch {
     size_t a_tc_stride;          // bytes per table in a_tc
     int* status;                 // set non-zero by a kernel whose bounded wait expired
     unsigned long long wait_ns;  // bound on each device-side wait (0: the default, 2 s)
+    float* part;                 // FP32 form: halves of split items [grid / 2 + 1][2][16][256] (null: no split)
+    int* part_cnt;               // [grid / 2 + 1] halves finished, reset to 0 by the second
     Seg segs[kMaxSegs];
 };
 

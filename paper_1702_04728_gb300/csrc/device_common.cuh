@@ -293,5 +293,30 @@ __device__ __forceinline__ void upchan_pass2(uint32_t tlane, int hh, float2 (&ac
     }
 }
 
+// The same with one float per sub-channel: the two fine channels of a SoA pair
+// are added before they join the running sum.
+__device__ __forceinline__ void upchan_pass2(uint32_t tlane, int hh, float (&acc)[kSub], float2* dump) {
+#pragma unroll 1
+    for (int cpi = 0; cpi < 4; ++cpi) {
+        cp y[16];
+        tmem_ld64(tlane + hh * 256 + 64 * cpi, y);
+        dft16(y);
+        if (dump) {
+#pragma unroll
+            for (int dd = 0; dd < 16; ++dd) {
+                const int c0 = 2 * cpi;
+                dump[(c0 + 8 * dd + kUp / 2) & (kUp - 1)] = make_float2(y[dd].re.x, y[dd].im.x);
+                dump[(c0 + 1 + 8 * dd + kUp / 2) & (kUp - 1)] = make_float2(y[dd].re.y, y[dd].im.y);
+            }
+        } else {
+#pragma unroll
+            for (int dd = 0; dd < 16; ++dd) {
+                const float2 p = fma2(y[dd].im, y[dd].im, mul2(y[dd].re, y[dd].re));
+                acc[(dd + 8) & 15] += p.x + p.y;
+            }
+        }
+    }
+}
+
 }  // namespace
 }  // namespace chimebf

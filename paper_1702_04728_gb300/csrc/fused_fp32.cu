@@ -1,22 +1,21 @@
 // Fused FP32 fan-beam kernel for sm_103a (arXiv 1702.04728, Sec. 3).
 //
-// One CTA (256 threads, one per SM) owns a work item = (channel segment,
-// output frame F, E-W beam j) and runs six passes over it, one per
-// (128-sample block, polarisation).  Arithmetic is packed FP32x2
-// (FFMA2 / FADD2) in structure-of-arrays form: every value is a pair of two
-// time samples (or two fine channels) that go through identical operations.
+// One CTA of 12 warps per SM owns a work item = (channel segment, output
+// frame F, E-W beam j) and runs six passes over it, one per (128-sample
+// block, polarisation).  Arithmetic is packed FP32x2 (FFMA2 / FADD2) in
+// structure-of-arrays form: every value is a pair of two time samples (or two
+// fine channels) that go through identical operations.
 //
-//  phase A (8 iterations per pass, 16 time samples each)
-//    * warp w loads the row pair tau = 16 w + 2 it + {0, 1} with 128-bit loads,
-//      unpacks the 4+4-bit nibbles (Table 1) exactly, and forms E-W beam j
-//      (Sec. 3) -- applied before the N-S transform, legal because both are
-//      linear and the phases do not depend on the feed;
-//    * the warp pair (2q, 2q+1) shares the phased feed lines of its 4 rows; the
-//      even warp computes the even bins (FFT256 of y), the odd warp the odd
-//      bins (FFT256 of y exp(-i pi n / 256)) of the zero-padded 512-point
-//      N-S FFT (Sec. 3.1), each as 16 x 16 with one shared-memory transpose;
-//      all 512 bins of every row land in a shared-memory row;
-//  gather + first up-channel pass (thread = N-S beam m)
+//  phase A, warps 0-7 (8 iterations per pass, 16 time samples each)
+//    * warp w takes the row pair tau = 16 w + 2 it + {0, 1}, staged in shared
+//      memory by cp.async, unpacks the 4+4-bit nibbles (Table 1) exactly and
+//      forms E-W beam j (Sec. 3) -- applied before the N-S transform, legal
+//      because both are linear and the phases do not depend on the feed;
+//    * lanes 0-15 compute the even bins (FFT256 of y), lanes 16-31 the odd
+//      bins (FFT256 of y exp(-i pi n / 256)) of the zero-padded 512-point N-S
+//      FFT (Sec. 3.1), each as 16 x 16 with one shared-memory transpose; all
+//      512 bins of the row pair land in the warp's row of a bin buffer;
+//  gather + first up-channel pass, warps 8-11 (thread = N-S beams m, m + 128)
 //    * bin L(m) of the clamp table (Eq. 1) is picked from the 8 rows of each
 //      time residue pair, an 8-point DFT runs in registers, and the twiddled
 //      result is parked in tensor memory (TMEM);
@@ -44,6 +43,50 @@ constexpr int kThreads = 32 * (kWarps + kCons);
 // for the consumers without waiting for each other.
 constexpr int kBarFull = 1, kBarCons = 3;
 
+// Register split (setmaxnreg): the launch gives every warp kRegLaunch registers per
+// thread; the producer warpgroups (warps 0-7) raise theirs to kRegProd and the
+// consumer warpgroup (warps 8-11) lowers its to kRegCons, within the same total.
+constexpr int kRegLaunch = 168, kRegProd = 176, kRegCons = 152;
+static_assert(kWarps * kRegProd + kCons * kRegCons <= (kWarps + kCons) * kRegLaunch,
+              "the register split must fit in the launch's register file share");
+
+// Work units.  A unit is an item (F, j) with all six passes, or one half of an
+// item: passes 0-2 or 3-5.  When the last round of items would leave at least
+// half of the CTAs idle, each item of that round becomes two half units on two
+// CTAs; the second to finish adds the two halves.  Every output is the sum of
+// the two halves (H0 + H1, one addition), whether or not its item was split,
+// so the result does not depend on how a request was batched.
+struct Units {
+    int n_full;     // items run whole: 0 .. n_full - 1
+    int n_units;    // n_full + 2 x (split items)
+};
+__device__ __forceinline__ Units make_units(int n_items, int grid, bool can_split) {
+    Units u{n_items, n_items};
+    if (can_split && n_items > grid) {
+        const int rem = n_items % grid;
+        if (rem > 0 && 2 * rem <= grid) {
+            u.n_full = n_items - rem;
+            u.n_units = u.n_full + 2 * rem;
+        }
+    }
+    return u;
+}
+// item, pass range [ps0, ps1) and half (-1: whole item) of unit `un`
+__device__ __forceinline__ void unit_of(const Units& u, int un, int& item, int& ps0, int& ps1, int& half) {
+    if (un < u.n_full) {
+        item = un;
+        ps0 = 0;
+        ps1 = kTds * kPol;
+        half = -1;
+    } else {
+        const int v = un - u.n_full;
+        item = u.n_full + (v >> 1);
+        half = v & 1;
+        ps0 = half * (kTds * kPol / 2);
+        ps1 = ps0 + kTds * kPol / 2;
+    }
+}
+
 // shared memory (float4 = one SoA pair: re0, re1, im0, im1)
 constexpr int kBinsF4 = kWarps * kBins;             // 8 row pairs x 512 bins (one of two buffers)
 constexpr int kYscF4 = kFeed;                        // per warp: its row pair's 256 phased feed lines
@@ -51,22 +94,13 @@ constexpr int kTbF4 = 2 * kFeed;                     // per warp: 2 halves x 16 
 constexpr int kRawB = 2 * kInput;                    // per producer warp and buffer: its two raw rows
 constexpr size_t kSmemBins = 2 * (size_t)kBinsF4 * 16;   // double-buffered across iterations
 constexpr size_t kSmemYsc = (size_t)kWarps * kYscF4 * 16;
-constexpr size_t kSmemRaw = 2 * (size_t)kWarps * kRawB;  // double-buffered raw rows (cp.async)
+constexpr size_t kSmemRaw = (size_t)kWarps * kRawB;      // raw rows (cp.async), one iteration ahead
 constexpr size_t kSmemLut = kNs * sizeof(int);
 constexpr size_t kSmemTw = 8 * 8 * 16;               // pair twiddles of the first up-channel pass
-constexpr size_t kSmemTotal = kSmemBins + kSmemYsc + kSmemRaw + kSmemLut + kSmemTw;
+constexpr size_t kSmemPark = (size_t)kSub * kNs * sizeof(float);   // first half of the current item
+constexpr size_t kSmemTotal = kSmemBins + kSmemYsc + kSmemRaw + kSmemLut + kSmemTw + kSmemPark;
 static_assert(kTbF4 == kBins, "a warp's transpose scratch is exactly its bin row");
 
-// ---------------------------------------------------------------------------
-// Phase A for one warp of a warp pair.
-//   in0/in1  the two rows of this warp's row pair (slot e of the pair)
-//   sel      byte permutation selecting polarisation pol of two feeds
-//   ysc      the pair's phased feed lines [2 slots][16 n2][16 n1] (swizzled)
-//   tb       this warp's transpose scratch [2 slots][16][16]
-//   bins2    bins of the pair's row pair slot 0 (slot 1 at + kBins)
-// e = warp & 1: the half of the padded FFT this warp computes, and the slot
-// of the row pair it loads.
-// ---------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t smem_sa(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
@@ -94,10 +128,13 @@ __device__ __forceinline__ cp lds_cp(uint32_t addr) {
 // (FFT256 of y exp(-i pi n / 256)) of the zero-padded 512-point N-S FFT, lane
 // n2 = lane & 15 in each half; `pt` holds that lane's twiddles.  Only warp-level
 // synchronisation: no other warp touches this warp's scratch.
-template <class BeforeTb>
+// Hooks: `after_ew` runs once in0/in1 have been consumed, `before_tb` before
+// the transpose scratch is first written, `after_tb` after the transposed
+// values are loaded (a slot for work that overlaps the last DFT).
+template <class AfterEw, class BeforeTb, class AfterTb>
 __device__ __forceinline__ void phase_a(const uint4 (&in0)[kCyl], const uint4 (&in1)[kCyl], uint32_t sel,
                                         const EwW& w, const PostTw& pt, uint32_t ysc, uint32_t tb, uint32_t row_bins,
-                                        int lane, BeforeTb before_tb) {
+                                        int lane, AfterEw after_ew, BeforeTb before_tb, AfterTb after_tb) {
     // unpack + E-W: lane holds feeds 8 lane .. 8 lane + 7 of both rows.  Feed n = 8 lane + 2k (+1)
     // sits at n2 = n & 15 = 8 (lane & 1) + 2k (+1), n1 = n >> 4 = lane >> 1; ysw(n2, n1) =
     // 16 n2 + (n1 ^ (n2 & 7) ^ 4 (n2 >> 3)) = 16 n2 + (((lane >> 1) ^ 4 (lane & 1)) ^ (n2 & 7)).
@@ -125,20 +162,25 @@ __device__ __forceinline__ void phase_a(const uint4 (&in0)[kCyl], const uint4 (&
         sts_cp((yw ^ (uint32_t)(16 * (2 * k))) + 256u * (2 * k), yA);
         sts_cp((yw ^ (uint32_t)(16 * (2 * k + 1))) + 256u * (2 * k + 1), yB);
     }
+    after_ew();
     __syncwarp();
 
     // half h = lane >> 4 of the padded FFT, lane handles n2 (both halves read the same lines):
     // ysw(n2, n1) = 16 n2 + (n1 ^ f), f = (n2 & 7) ^ 4 (n2 >> 3)
     const int h = lane >> 4, n2 = lane & 15;
     const uint32_t yr = ysc + 16u * (uint32_t)(16 * n2 + ((n2 & 7) ^ (4 * (n2 >> 3))));
+    // loads in the order the first radix-4 stage of dft16 consumes them
     cp v[16];
 #pragma unroll
-    for (int n1 = 0; n1 < 16; ++n1) v[n1] = lds_cp(yr ^ (uint32_t)(16 * n1));
+    for (int q = 0; q < 16; ++q) {
+        const int n1 = 4 * (q & 3) + (q >> 2);
+        v[n1] = lds_cp(yr ^ (uint32_t)(16 * n1));
+    }
     if (h) {
         // odd bins: input times exp(-i pi n / 256) = exp(-2 pi i n1 / 32) * exp(-2 pi i n2 / 512);
         // the second factor is folded into the per-lane twiddles
 #pragma unroll
-        for (int n1 = 1; n1 < 16; ++n1) v[n1] = cmulp(v[n1], bc(cos32(n1)), bc(-sin32(n1)));
+        for (int n1 = 1; n1 < 16; ++n1) v[n1] = twiddle<32>(v[n1], n1);
     }
     dft16(v);
 #pragma unroll
@@ -157,8 +199,12 @@ __device__ __forceinline__ void phase_a(const uint4 (&in0)[kCyl], const uint4 (&
     {
         const uint32_t tr_ = tbl + 16u * (uint32_t)k1;
 #pragma unroll
-        for (int r = 0; r < 16; ++r) v[r] = lds_cp((tr_ ^ (uint32_t)(16 * (r & 7))) + 256u * r);
+        for (int q = 0; q < 16; ++q) {
+            const int r = 4 * (q & 3) + (q >> 2);
+            v[r] = lds_cp((tr_ ^ (uint32_t)(16 * (r & 7))) + 256u * r);
+        }
     }
+    after_tb();
     dft16(v);
     // every lane is done with the scratch before the bins (which may share its memory) are written
     __syncwarp();
@@ -209,9 +255,11 @@ __global__ void __launch_bounds__(kThreads, 1) fused_fp32_kernel(const __grid_co
     unsigned char* raw_all = smem + kSmemBins + kSmemYsc;
     int* lut_s = reinterpret_cast<int*>(smem + kSmemBins + kSmemYsc + kSmemRaw);
     float4* tw_s = reinterpret_cast<float4*>(smem + kSmemBins + kSmemYsc + kSmemRaw + kSmemLut);
+    float* park_s = reinterpret_cast<float*>(smem + kSmemBins + kSmemYsc + kSmemRaw + kSmemLut + kSmemTw);
     __shared__ uint32_t tmem_base_s;
     __shared__ __align__(8) uint64_t empty_s[2];
     __shared__ int expired_s;
+    __shared__ int second_s;          // this CTA finished the second half of a split item
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     constexpr int kAll = kThreads;
@@ -240,14 +288,20 @@ __global__ void __launch_bounds__(kThreads, 1) fused_fp32_kernel(const __grid_co
     constexpr int kPasses = kTds * kPol;
     const unsigned long long wlim = bt.wait_ns ? bt.wait_ns : kWaitNs;
 
+    const Units units = make_units(bt.n_items, (int)gridDim.x, !kDump && bt.part != nullptr);
+    static_assert(kTds * kPol == 6, "an item is two halves of three passes");
+
     if (warp < kWarps) {
         // ---------------------------------- producers ----------------------------------
+        asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" :: "n"(kRegProd) : "memory");
         const uint32_t ysc_sa = smem_sa(ysc_all + warp * kYscF4);
         const uint32_t raw_sa = smem_sa(raw_all) + (uint32_t)(warp * kRawB) + 16u * lane;
         PostTw pt;
         load_post(bt.tw512, lane & 15, lane >> 4, pt);
         uint32_t g = 0;                                   // iterations done by this CTA
-        for (int item = blockIdx.x; item < bt.n_items; item += gridDim.x) {
+        for (int un = blockIdx.x; un < units.n_units; un += gridDim.x) {
+            int item, ps0, ps1, half;
+            unit_of(units, un, item, ps0, ps1, half);
             int sgi = 0;
             while (sgi + 1 < bt.n_segs && bt.segs[sgi + 1].item_begin <= item) ++sgi;
             const Seg& sg = bt.segs[sgi];
@@ -256,59 +310,77 @@ __global__ void __launch_bounds__(kThreads, 1) fused_fp32_kernel(const __grid_co
             EwW w;
             load_ew_frame(sg, bt.ew, F, j, w);
             const long long row0 = (long long)F * kFrame + 16 * warp;
-            // this warp's two rows of iteration (ps, it) into raw buffer rb (own bytes only)
-            auto fetch = [&](int ps, int it, uint32_t rb) {
+            // this warp's two rows of iteration (ps, it) into its raw buffer (own bytes only)
+            auto fetch = [&](int ps, int it) {
                 const long long r = row0 + (ps >> 1) * kUp + 2 * it;
                 const uint8_t* p0 = frame_row(sg, r) + 16 * lane;
                 const uint8_t* p1 = frame_row(sg, r + 1) + 16 * lane;
-                const uint32_t d = raw_sa + rb * (uint32_t)(kWarps * kRawB);
 #pragma unroll
                 for (int c = 0; c < kCyl; ++c) {
-                    cp16(d + c * (kFeed * kPol), p0 + c * (kFeed * kPol));
-                    cp16(d + kInput + c * (kFeed * kPol), p1 + c * (kFeed * kPol));
+                    cp16(raw_sa + c * (kFeed * kPol), p0 + c * (kFeed * kPol));
+                    cp16(raw_sa + kInput + c * (kFeed * kPol), p1 + c * (kFeed * kPol));
                 }
                 cp_commit();
             };
-            fetch(0, 0, g & 1u);
-            for (int ps = 0; ps < kPasses; ++ps) {
+            auto load_raw = [&](uint4 (&r0)[kCyl], uint4 (&r1)[kCyl]) {
+#pragma unroll
+                for (int c = 0; c < kCyl; ++c) {
+                    r0[c] = lds_u4(raw_sa + c * (kFeed * kPol));
+                    r1[c] = lds_u4(raw_sa + kInput + c * (kFeed * kPol));
+                }
+            };
+            // The current iteration's raw words are in registers.  Once the unpack has
+            // consumed them, the next iteration's rows are copied into the raw buffer, and
+            // they are read into registers during this iteration's last DFT.
+            uint4 in0[kCyl], in1[kCyl];
+            fetch(ps0, 0);
+            cp_wait<0>();
+            load_raw(in0, in1);
+            for (int ps = ps0; ps < ps1; ++ps) {
                 const int pol = ps & 1;
                 const uint32_t sel = 0x4400u | ((2u + pol) << 4) | (uint32_t)pol;
 #pragma unroll 1
                 for (int it = 0; it < 8; ++it, ++g) {
                     const uint32_t b = g & 1u;
-                    // rows of the next iteration of this item, then this iteration's rows
-                    if (it < 7 || ps + 1 < kPasses) {
-                        fetch(it < 7 ? ps : ps + 1, it < 7 ? it + 1 : 0, b ^ 1u);
-                        cp_wait<1>();
-                    } else {
-                        cp_wait<0>();
-                    }
-                    const uint32_t rs = raw_sa + b * (uint32_t)(kWarps * kRawB);
-                    uint4 in0[kCyl], in1[kCyl];
-#pragma unroll
-                    for (int c = 0; c < kCyl; ++c) {
-                        in0[c] = lds_u4(rs + c * (kFeed * kPol));
-                        in1[c] = lds_u4(rs + kInput + c * (kFeed * kPol));
-                    }
+                    const bool more = it < 7 || ps + 1 < ps1;
+                    uint4 nx0[kCyl], nx1[kCyl];
                     const uint32_t row_bins = smem_sa(bins_all + b * kBinsF4 + warp * kBins);
-                    phase_a(in0, in1, sel, w, pt, ysc_sa, row_bins, row_bins, lane, [&] {
+                    phase_a(in0, in1, sel, w, pt, ysc_sa, row_bins, row_bins, lane,
+                            [&] {
+                                if (more) fetch(it < 7 ? ps : ps + 1, it < 7 ? it + 1 : 0);
+                            },
+                            [&] {
                                 // buffer b is free once the consumers gathered it two iterations ago
                                 // (release number g / 2 - 1 of buffer b)
                                 if (g >= 2 && !mbar_wait(empty0 + 8u * b, ((g >> 1) + 1u) & 1u, wlim))
                                     expired_s = 1;
+                            },
+                            [&] {
+                                if (more) {
+                                    cp_wait<0>();
+                                    load_raw(nx0, nx1);
+                                }
                             });
                     bar_arrive_n(kBarFull + (int)b, kAll);
+#pragma unroll
+                    for (int c = 0; c < kCyl; ++c) {
+                        in0[c] = nx0[c];
+                        in1[c] = nx1[c];
+                    }
                 }
             }
         }
     } else {
         // ---------------------------------- consumers ----------------------------------
+        asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" :: "n"(kRegCons) : "memory");
         const int cq = warp - kWarps;                    // TMEM lane quarter
         const int ctid = tid - 32 * kWarps;
         const uint32_t tlane = tmem + (static_cast<uint32_t>(32 * cq) << 16);
         const int m0 = 32 * cq + lane;                   // bins m0 (half 0) and m0 + 128 (half 1)
         uint32_t g = 0;
-        for (int item = blockIdx.x; item < bt.n_items; item += gridDim.x) {
+        for (int un = blockIdx.x; un < units.n_units; un += gridDim.x) {
+            int item, ps0, ps1, half;
+            unit_of(units, un, item, ps0, ps1, half);
             int sgi = 0;
             while (sgi + 1 < bt.n_segs && bt.segs[sgi + 1].item_begin <= item) ++sgi;
             const Seg& sg = bt.segs[sgi];
@@ -318,13 +390,16 @@ __global__ void __launch_bounds__(kThreads, 1) fused_fp32_kernel(const __grid_co
             for (int i = ctid; i < kNs; i += 32 * kCons) lut_s[i] = bt.lut[sg.table * kNs + i];
             bar_sync_n(kBarCons, 32 * kCons);
             const int Lsw0 = bsw(lut_s[m0]), Lsw1 = bsw(lut_s[m0 + 128]);
-            float2 acc0[kSub], acc1[kSub];
+            // output addresses are formed where they are used (registers are tight here)
+            auto out0 = [&] { return sg.out + (long long)(kNs * j + m0) * sg.beam_stride + F; };
+            auto out1 = [&] { return sg.out + (long long)(kNs * j + m0 + 128) * sg.beam_stride + F; };
+            float acc0[kSub], acc1[kSub];
 #pragma unroll
             for (int s2 = 0; s2 < kSub; ++s2) {
-                acc0[s2] = make_float2(0.f, 0.f);
-                acc1[s2] = make_float2(0.f, 0.f);
+                acc0[s2] = 0.f;
+                acc1[s2] = 0.f;
             }
-            for (int ps = 0; ps < kPasses; ++ps) {
+            for (int ps = ps0; ps < ps1; ++ps) {
                 const int blk = ps >> 1, pol = ps & 1;
 #pragma unroll 1
                 for (int it = 0; it < 8; ++it, ++g) {
@@ -360,14 +435,68 @@ __global__ void __launch_bounds__(kThreads, 1) fused_fp32_kernel(const __grid_co
                 upchan_pass2(tlane, 1, acc1, kDump ? bt.dump + dbase + (long long)(m0 + 128) * kUp : nullptr);
                 // the next pass's gathers overwrite these TMEM columns in this warp's program order
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if constexpr (!kDump) {
+                    if (half < 0 && ps == kTds * kPol / 2 - 1) {
+                        // whole item: H0 (passes 0-2) parks in shared memory until H1 is done
+                        // (each thread reads back only its own words)
+                        float* pk = park_s;
+#pragma unroll
+                        for (int s2 = 0; s2 < kSub; ++s2) {
+                            pk[s2 * kNs + m0] = acc0[s2];
+                            pk[s2 * kNs + m0 + 128] = acc1[s2];
+                            acc0[s2] = 0.f;
+                            acc1[s2] = 0.f;
+                        }
+                    }
+                }
             }
             if constexpr (!kDump) {
-                float* o0 = sg.out + (long long)(kNs * j + m0) * sg.beam_stride + F;
-                float* o1 = sg.out + (long long)(kNs * j + m0 + 128) * sg.beam_stride + F;
+                if (half < 0) {
+                    // all loads before the first store: the stores could alias them as far as
+                    // the compiler knows, and would otherwise serialise the loads
+                    const float* pk = park_s;
+                    float h[kSub];
 #pragma unroll
-                for (int s2 = 0; s2 < kSub; ++s2) {
-                    o0[(long long)s2 * sg.sub_stride] = acc0[s2].x + acc0[s2].y;
-                    o1[(long long)s2 * sg.sub_stride] = acc1[s2].x + acc1[s2].y;
+                    for (int s2 = 0; s2 < kSub; ++s2) h[s2] = pk[s2 * kNs + m0];
+                    float* o = out0();
+#pragma unroll
+                    for (int s2 = 0; s2 < kSub; ++s2) o[(long long)s2 * sg.sub_stride] = h[s2] + acc0[s2];
+#pragma unroll
+                    for (int s2 = 0; s2 < kSub; ++s2) h[s2] = pk[s2 * kNs + m0 + 128];
+                    o = out1();
+#pragma unroll
+                    for (int s2 = 0; s2 < kSub; ++s2) o[(long long)s2 * sg.sub_stride] = h[s2] + acc1[s2];
+                } else {
+                    // half unit: publish this half, then the second of the two halves to
+                    // finish adds them (a fence and a counter; nothing waits)
+                    const int slot = item - units.n_full;
+                    float* mine = bt.part + ((size_t)slot * 2 + half) * (kSub * kNs);
+#pragma unroll
+                    for (int s2 = 0; s2 < kSub; ++s2) {
+                        mine[s2 * kNs + m0] = acc0[s2];
+                        mine[s2 * kNs + m0 + 128] = acc1[s2];
+                    }
+                    __threadfence();
+                    bar_sync_n(kBarCons, 32 * kCons);
+                    if (ctid == 0) second_s = atomicAdd(&bt.part_cnt[slot], 1);
+                    bar_sync_n(kBarCons, 32 * kCons);
+                    if (second_s) {
+                        __threadfence();
+                        // H0 + H1 in either order: one addition of two terms is exact-commutative
+                        const float* other = bt.part + ((size_t)slot * 2 + (half ^ 1)) * (kSub * kNs);
+                        float h[kSub];
+#pragma unroll
+                        for (int s2 = 0; s2 < kSub; ++s2) h[s2] = __ldcg(other + s2 * kNs + m0);
+                        float* o = out0();
+#pragma unroll
+                        for (int s2 = 0; s2 < kSub; ++s2) o[(long long)s2 * sg.sub_stride] = acc0[s2] + h[s2];
+#pragma unroll
+                        for (int s2 = 0; s2 < kSub; ++s2) h[s2] = __ldcg(other + s2 * kNs + m0 + 128);
+                        o = out1();
+#pragma unroll
+                        for (int s2 = 0; s2 < kSub; ++s2) o[(long long)s2 * sg.sub_stride] = acc1[s2] + h[s2];
+                        if (ctid == 0) bt.part_cnt[slot] = 0;      // ready for the next launch
+                    }
                 }
             }
         }
@@ -405,7 +534,7 @@ __global__ void __launch_bounds__(64) debug_beams_kernel(const uint8_t* __restri
     load_row(vin + rb * kInput, lane, in1);
     const uint32_t sel = 0x4400u | ((2u + pol) << 4) | (uint32_t)pol;
     phase_a(in0, in1, sel, w, pt, smem_sa(ysc + e * kYscF4), smem_sa(tbs[warp]), smem_sa(bins2 + e * kBins), lane,
-            [] {});
+            [] {}, [] {}, [] {});
     __syncthreads();
     for (int i = threadIdx.x; i < 4 * kNs; i += 64) {
         const int r = i >> 8, mm = i & 255;          // r: row 0..3 = slot (r >> 1), element (r & 1)
@@ -427,10 +556,23 @@ __global__ void debug_unpack_kernel(const uint8_t* __restrict__ in, float2* __re
 
 }  // namespace
 
+// Shared-memory opt-in, and a check that the compiled kernel was given the
+// registers per thread the setmaxnreg split assumes: with fewer, the producers'
+// increase could not be granted, so such a build is refused instead of launched.
+template <bool kDump>
+cudaError_t prepare_fp32() {
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, fused_fp32_kernel<kDump>);
+    if (e != cudaSuccess) return e;
+    if (fa.numRegs < kRegLaunch) return cudaErrorInvalidConfiguration;
+    return cudaFuncSetAttribute(fused_fp32_kernel<kDump>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)kSmemTotal);
+}
+
 cudaError_t fused_fp32_launch(const Batch& b, int grid, cudaStream_t s) {
     if (b.n_items <= 0) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(fused_fp32_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)kSmemTotal);
+    if (b.part && grid > 2 * kMaxSplit) return cudaErrorInvalidValue;
+    cudaError_t e = prepare_fp32<false>();
     if (e != cudaSuccess) return e;
     fused_fp32_kernel<false><<<grid, kThreads, kSmemTotal, s>>>(b);
     return cudaGetLastError();
@@ -438,8 +580,7 @@ cudaError_t fused_fp32_launch(const Batch& b, int grid, cudaStream_t s) {
 
 cudaError_t fused_fp32_dump_launch(const Batch& b, int grid, cudaStream_t s) {
     if (b.n_items <= 0) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(fused_fp32_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)kSmemTotal);
+    cudaError_t e = prepare_fp32<true>();
     if (e != cudaSuccess) return e;
     fused_fp32_kernel<true><<<grid, kThreads, kSmemTotal, s>>>(b);
     return cudaGetLastError();

@@ -118,6 +118,8 @@ struct bf_plan_s {
     int* d_delays = nullptr;                  // dedispersion delay table (grown on demand)
     size_t delays_cap = 0;
     int* d_status = nullptr;
+    float* d_part = nullptr;                  // FP32 form: halves of split items (see Batch::part)
+    int* d_part_cnt = nullptr;
 
     std::mutex mu;
     std::condition_variable cv;
@@ -278,6 +280,8 @@ Batch make_batch(const bf_plan_s* p) {
     b.a_tc = p->d_atc;
     b.a_tc_stride = p->terms ? tc_a_bytes(p->terms) : 0;
     b.status = p->d_status;
+    b.part = p->d_part;
+    b.part_cnt = p->d_part_cnt;
     return b;
 }
 
@@ -650,6 +654,13 @@ int bf_plan(const bf_config* cfg, bf_plan_t* out) {
     CK(cudaHostAlloc(&p->h_status, sizeof(int), cudaHostAllocMapped));
     *p->h_status = 0;
     CK(cudaHostGetDevicePointer(&p->d_status, p->h_status, 0));
+    if (!p->terms && p->grid <= 2 * kMaxSplit) {
+        // a launch splits at most grid / 2 items: two halves of 16 x 256 floats each
+        const size_t slots = (size_t)p->grid / 2 + 1;
+        CK(cudaMalloc(&p->d_part, slots * 2 * kSub * kNs * sizeof(float)));
+        CK(cudaMalloc(&p->d_part_cnt, slots * sizeof(int)));
+        CK(cudaMemset(p->d_part_cnt, 0, slots * sizeof(int)));
+    }
 
     if (p->cfg.mode == BF_MODE_SERVING) {
         bf_plan_s* raw = p.get();
@@ -795,6 +806,8 @@ int bf_destroy(bf_plan_t p) {
     cudaFree(p->d_ew);
     cudaFree(p->d_tw512);
     cudaFree(p->d_tw128);
+    cudaFree(p->d_part);
+    cudaFree(p->d_part_cnt);
     if (p->d_atc) cudaFree(p->d_atc);
     if (p->d_delays) cudaFree(p->d_delays);
     if (p->h_status) cudaFreeHost(p->h_status);

@@ -167,6 +167,37 @@ def test_node_slice_full_size_sampled(plan):
     assert_rel(got, ref)
 
 
+def test_tail_split_items_match_whole_items(plan):
+    """A launch whose last round of items would leave at least half of the CTAs
+    idle runs each item of that round as two half units on two CTAs.  The output
+    must equal, bit for bit, a run of the same stream in two requests whose
+    items all run whole, and the oracle within tolerance."""
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    nf1, nf2 = sms // 4, 5
+    items = 4 * (nf1 + nf2)
+    rem = items % sms
+    if not (items > sms and 0 < rem and 2 * rem <= sms):
+        pytest.skip(f"{sms} SMs: no tail split for {items} items")
+    freq = 615e6
+    T = 384 * (nf1 + nf2)
+    raw = rand_raw((1, T, 2048), seed=31, lo=-7)
+    whole = plan.run(dev(raw), [freq], stream_id=2000)
+    assert whole.shape == (1024, 16, nf1 + nf2)
+    parts = []
+    for a, b, flags in ((0, 384 * nf1, 0), (384 * nf1, T, B.BF_END_OF_STREAM)):
+        nf = (b - a) // 384
+        out = torch.empty(1024, 16, nf, dtype=torch.float32, device="cuda")
+        _, t = plan.submit(dev(raw[:, a:b]), [freq], out, stream_id=2001, flags=flags, n_samples=b - a)
+        assert plan.poll(t) == (B.BF_OK, nf)
+        parts.append(out)
+    assert torch.equal(torch.cat(parts, dim=2), whole)
+    got = whole.cpu().numpy()
+    rng = np.random.default_rng(33)
+    picks = [(0, int(rng.integers(1024)), fr) for fr in range(nf1 - 1, nf1 + nf2) for _ in range(3)]
+    ref = O.beamform_sample(raw, [freq], picks)
+    assert_rel(np.stack([got[b, 0:16, fr] for _, b, fr in picks]), ref)
+
+
 @pytest.mark.parametrize("form", [B.BF_FP32_FFT, B.BF_TC_DFT256])
 def test_more_channels_than_one_launch_holds(built_lib, form):
     """200 channels (segments) exceed one launch's 160 segment descriptors, so the
