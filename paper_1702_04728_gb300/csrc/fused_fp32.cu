@@ -343,7 +343,6 @@ __global__ void __launch_bounds__(kThreads, 1) fused_fp32_kernel(const __grid_co
                 for (int it = 0; it < 8; ++it, ++g) {
                     const uint32_t b = g & 1u;
                     const bool more = it < 7 || ps + 1 < ps1;
-                    uint4 nx0[kCyl], nx1[kCyl];
                     const uint32_t row_bins = smem_sa(bins_all + b * kBinsF4 + warp * kBins);
                     phase_a(in0, in1, sel, w, pt, ysc_sa, row_bins, row_bins, lane,
                             [&] {
@@ -356,17 +355,13 @@ __global__ void __launch_bounds__(kThreads, 1) fused_fp32_kernel(const __grid_co
                                     expired_s = 1;
                             },
                             [&] {
+                                // in0 / in1 were consumed by the unpack: the next rows replace them
                                 if (more) {
                                     cp_wait<0>();
-                                    load_raw(nx0, nx1);
+                                    load_raw(in0, in1);
                                 }
                             });
                     bar_arrive_n(kBarFull + (int)b, kAll);
-#pragma unroll
-                    for (int c = 0; c < kCyl; ++c) {
-                        in0[c] = nx0[c];
-                        in1[c] = nx1[c];
-                    }
                 }
             }
         }
