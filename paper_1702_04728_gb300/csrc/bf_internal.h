@@ -55,8 +55,10 @@ struct Batch {
     size_t a_tc_stride;          // bytes per table in a_tc
     int* status;                 // set non-zero by a kernel whose bounded wait expired
     unsigned long long wait_ns;  // bound on each device-side wait (0: the default, 2 s)
-    float* part;                 // FP32 form: halves of split items [grid / 2 + 1][2][16][256] (null: no split)
-    int* part_cnt;               // [grid / 2 + 1] halves finished, reset to 0 by the second
+    float* part;                 // halves of split items [grid / 2 + 1][2][16][256] (null: no split)
+    unsigned long long* part_tok;    // [grid / 2 + 1][256] handshake tokens (2 x epoch + half)
+    unsigned long long epoch;        // this launch's number within the plan (from 1)
+    float* park;                 // tensor-core form: first half of each CTA's item [grid][16][256]
     Seg segs[kMaxSegs];
 };
 

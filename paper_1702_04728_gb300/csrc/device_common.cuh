@@ -255,6 +255,56 @@ __device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(mbar) : "memory");
 }
 
+// Work units.  A unit is an item (F, j) with all six passes, or one half of an
+// item: passes 0-2 or 3-5.  When the last round of items would leave at least
+// half of the CTAs idle, each item of that round becomes two half units on two
+// CTAs; the second to finish adds the two halves.  Every output is the sum of
+// the two halves (H0 + H1, one addition), whether or not its item was split,
+// so the result does not depend on how a request was batched.
+struct Units {
+    int n_full;     // items run whole: 0 .. n_full - 1
+    int n_units;    // n_full + 2 x (split items)
+};
+__device__ __forceinline__ Units make_units(int n_items, int grid, bool can_split) {
+    Units u{n_items, n_items};
+    if (can_split && n_items > grid) {
+        const int rem = n_items % grid;
+        if (rem > 0 && 2 * rem <= grid) {
+            u.n_full = n_items - rem;
+            u.n_units = u.n_full + 2 * rem;
+        }
+    }
+    return u;
+}
+// item, pass range [ps0, ps1) and half (-1: whole item) of unit `un`
+__device__ __forceinline__ void unit_of(const Units& u, int un, int& item, int& ps0, int& ps1, int& half) {
+    if (un < u.n_full) {
+        item = un;
+        ps0 = 0;
+        ps1 = kTds * kPol;
+        half = -1;
+    } else {
+        const int v = un - u.n_full;
+        item = u.n_full + (v >> 1);
+        half = v & 1;
+        ps0 = half * (kTds * kPol / 2);
+        ps1 = ps0 + kTds * kPol / 2;
+    }
+}
+
+// Split items: the two halves of an item run on two CTAs.  A thread publishes
+// its half's partial sums, then swaps its token (launch epoch x 2 + half) into
+// its slot; the thread that finds its partner's token from the same launch there
+// is the second of the two and adds the halves.  Tokens of earlier launches never
+// match, so an abandoned launch leaves nothing to clean up, and nothing waits.
+__device__ __forceinline__ bool second_half(unsigned long long* tok, unsigned long long epoch, int half) {
+    __threadfence();                                   // the published sums before the token
+    const unsigned long long mine = 2ull * epoch + (unsigned long long)half;
+    if (atomicExch(tok, mine) != (mine ^ 1ull)) return false;
+    __threadfence();                                   // the partner's sums after its token
+    return true;
+}
+
 // CTA barrier that also orders tensor-memory accesses across it.
 __device__ __forceinline__ void cta_sync() {
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");

@@ -50,43 +50,6 @@ constexpr int kRegLaunch = 168, kRegProd = 176, kRegCons = 152;
 static_assert(kWarps * kRegProd + kCons * kRegCons <= (kWarps + kCons) * kRegLaunch,
               "the register split must fit in the launch's register file share");
 
-// Work units.  A unit is an item (F, j) with all six passes, or one half of an
-// item: passes 0-2 or 3-5.  When the last round of items would leave at least
-// half of the CTAs idle, each item of that round becomes two half units on two
-// CTAs; the second to finish adds the two halves.  Every output is the sum of
-// the two halves (H0 + H1, one addition), whether or not its item was split,
-// so the result does not depend on how a request was batched.
-struct Units {
-    int n_full;     // items run whole: 0 .. n_full - 1
-    int n_units;    // n_full + 2 x (split items)
-};
-__device__ __forceinline__ Units make_units(int n_items, int grid, bool can_split) {
-    Units u{n_items, n_items};
-    if (can_split && n_items > grid) {
-        const int rem = n_items % grid;
-        if (rem > 0 && 2 * rem <= grid) {
-            u.n_full = n_items - rem;
-            u.n_units = u.n_full + 2 * rem;
-        }
-    }
-    return u;
-}
-// item, pass range [ps0, ps1) and half (-1: whole item) of unit `un`
-__device__ __forceinline__ void unit_of(const Units& u, int un, int& item, int& ps0, int& ps1, int& half) {
-    if (un < u.n_full) {
-        item = un;
-        ps0 = 0;
-        ps1 = kTds * kPol;
-        half = -1;
-    } else {
-        const int v = un - u.n_full;
-        item = u.n_full + (v >> 1);
-        half = v & 1;
-        ps0 = half * (kTds * kPol / 2);
-        ps1 = ps0 + kTds * kPol / 2;
-    }
-}
-
 // shared memory (float4 = one SoA pair: re0, re1, im0, im1)
 constexpr int kBinsF4 = kWarps * kBins;             // 8 row pairs x 512 bins (one of two buffers)
 constexpr int kYscF4 = kFeed;                        // per warp: its row pair's 256 phased feed lines
@@ -259,7 +222,6 @@ __global__ void __launch_bounds__(kThreads, 1) fused_fp32_kernel(const __grid_co
     __shared__ uint32_t tmem_base_s;
     __shared__ __align__(8) uint64_t empty_s[2];
     __shared__ int expired_s;
-    __shared__ int second_s;          // this CTA finished the second half of a split item
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     constexpr int kAll = kThreads;
@@ -462,8 +424,8 @@ __global__ void __launch_bounds__(kThreads, 1) fused_fp32_kernel(const __grid_co
 #pragma unroll
                     for (int s2 = 0; s2 < kSub; ++s2) o[(long long)s2 * sg.sub_stride] = h[s2] + acc1[s2];
                 } else {
-                    // half unit: publish this half, then the second of the two halves to
-                    // finish adds them (a fence and a counter; nothing waits)
+                    // half unit: publish this half; the second of the two halves to finish
+                    // adds them (per thread: bins m0 and m0 + 128)
                     const int slot = item - units.n_full;
                     float* mine = bt.part + ((size_t)slot * 2 + half) * (kSub * kNs);
 #pragma unroll
@@ -471,12 +433,7 @@ __global__ void __launch_bounds__(kThreads, 1) fused_fp32_kernel(const __grid_co
                         mine[s2 * kNs + m0] = acc0[s2];
                         mine[s2 * kNs + m0 + 128] = acc1[s2];
                     }
-                    __threadfence();
-                    bar_sync_n(kBarCons, 32 * kCons);
-                    if (ctid == 0) second_s = atomicAdd(&bt.part_cnt[slot], 1);
-                    bar_sync_n(kBarCons, 32 * kCons);
-                    if (second_s) {
-                        __threadfence();
+                    if (second_half(bt.part_tok + (size_t)slot * kNs + m0, bt.epoch, half)) {
                         // H0 + H1 in either order: one addition of two terms is exact-commutative
                         const float* other = bt.part + ((size_t)slot * 2 + (half ^ 1)) * (kSub * kNs);
                         float h[kSub];
@@ -490,7 +447,6 @@ __global__ void __launch_bounds__(kThreads, 1) fused_fp32_kernel(const __grid_co
                         o = out1();
 #pragma unroll
                         for (int s2 = 0; s2 < kSub; ++s2) o[(long long)s2 * sg.sub_stride] = acc1[s2] + h[s2];
-                        if (ctid == 0) bt.part_cnt[slot] = 0;      // ready for the next launch
                     }
                 }
             }

@@ -373,6 +373,13 @@ __global__ void __launch_bounds__(TcCfg<TERMS>::NT, 1) fused_tc_kernel(const __g
     const uint32_t tmem = tmem_base_s;
     constexpr int PASSES = kTds * kPol;
     const unsigned long long wlim = bt.wait_ns ? bt.wait_ns : kWaitNs;
+    // Tail items are split for the 1- and 3-term forms; the 2-term form, whose builders are
+    // the most register- and L1-bound, measured slower with the extra epilogue.
+    constexpr bool SPLIT = MODE == 0 && TERMS != 2;
+    const Units units = make_units(bt.n_items, (int)gridDim.x, SPLIT);
+    // this CTA's units are blockIdx.x + k gridDim.x: whole items first, then at most one half
+    auto my_count = [&](int n) { return n > (int)blockIdx.x ? (n - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0; };
+    const int n_my_whole = my_count(units.n_full), n_my_units = my_count(units.n_units);
 
     if (!producer) {
         // ------------------------------ MMA / copy warp ------------------------------
@@ -381,14 +388,17 @@ __global__ void __launch_bounds__(TcCfg<TERMS>::NT, 1) fused_tc_kernel(const __g
             uint32_t p_bfull = 0, p_afull = 0, p_aempty = 0, p_tfree = 0;
             long long c = 0;                                  // global chunk number
             long long c_copy = 0;                             // next twiddle chunk to copy
-            const long long n_my_items = bt.n_items > (int)blockIdx.x
-                                             ? (bt.n_items - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
-            const long long total = n_my_items * PASSES * C::NCH;
+            const long long whole_chunks = (long long)n_my_whole * PASSES * C::NCH;
+            const long long total = whole_chunks + (long long)(n_my_units - n_my_whole) * (PASSES / 2) * C::NCH;
             // table of the item that chunk cc belongs to; items only move forward, so
             // the segment search resumes where the previous lookup stopped
             int seg_cursor = 0;
             auto table_of = [&](long long cc) {
-                const int it = (int)blockIdx.x + (int)(cc / (PASSES * C::NCH)) * (int)gridDim.x;
+                const int k = cc < whole_chunks
+                                  ? (int)(cc / (PASSES * C::NCH))
+                                  : n_my_whole + (int)((cc - whole_chunks) / ((PASSES / 2) * C::NCH));
+                int it, ps0, ps1, half;
+                unit_of(units, (int)blockIdx.x + k * (int)gridDim.x, it, ps0, ps1, half);
                 while (seg_cursor + 1 < bt.n_segs && bt.segs[seg_cursor + 1].item_begin <= it) ++seg_cursor;
                 return bt.segs[seg_cursor].table;
             };
@@ -457,7 +467,9 @@ __global__ void __launch_bounds__(TcCfg<TERMS>::NT, 1) fused_tc_kernel(const __g
         uint32_t p_bempty = 0, p_acc = 0;
         long long c = 0;
         bool ok = true;
-        for (int item = blockIdx.x; item < bt.n_items && ok; item += gridDim.x) {
+        for (int k = 0; k < n_my_units && ok; ++k) {
+            int item, ps0, ps1, half;
+            unit_of(units, (int)blockIdx.x + k * (int)gridDim.x, item, ps0, ps1, half);
             int sgi = 0;
             while (sgi + 1 < bt.n_segs && bt.segs[sgi + 1].item_begin <= item) ++sgi;
             const Seg& sg = bt.segs[sgi];
@@ -469,8 +481,8 @@ __global__ void __launch_bounds__(TcCfg<TERMS>::NT, 1) fused_tc_kernel(const __g
 #pragma unroll
             for (int q = 0; q < kSub; ++q) acc[q] = make_float2(0.f, 0.f);
             RawB<TERMS> raw;
-            load_b<TERMS>(sg, (long long)F * kFrame, 0, tid, raw);
-            for (int ps = 0; ps < PASSES && ok; ++ps) {
+            load_b<TERMS>(sg, (long long)F * kFrame + (ps0 >> 1) * kUp, 0, tid, raw);
+            for (int ps = ps0; ps < ps1 && ok; ++ps) {
                 const int blk = ps >> 1, pol = ps & 1;
                 const uint32_t sel = 0x4400u | ((2u + pol) << 4) | (uint32_t)pol;
                 for (int kc = 0; kc < C::NCH && ok; ++kc, ++c) {
@@ -483,7 +495,7 @@ __global__ void __launch_bounds__(TcCfg<TERMS>::NT, 1) fused_tc_kernel(const __g
                     unsigned char* sb_lo = sb_hi + C::OPER;
                     RawB<TERMS> cur = raw;
                     const bool last = kc + 1 == C::NCH;
-                    if (!last || ps + 1 < PASSES) {
+                    if (!last || ps + 1 < ps1) {
                         const int nblk = last ? ((ps + 1) >> 1) : blk;
                         load_b<TERMS>(sg, (long long)F * kFrame + nblk * kUp, last ? 0 : kc + 1, tid, raw);
                     }
@@ -518,12 +530,51 @@ __global__ void __launch_bounds__(TcCfg<TERMS>::NT, 1) fused_tc_kernel(const __g
                 asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                 __syncwarp();
                 if (lane == 0) mbar_arrive(tfree);
+                if constexpr (SPLIT) {
+                    if (half < 0 && ps == PASSES / 2 - 1) {
+                        // whole item: H0 (passes 0-2) parks in this CTA's slot (coalesced)
+                        // until H1 is done
+                        float* pk = bt.park + (size_t)blockIdx.x * (kSub * kNs) + m;
+#pragma unroll
+                        for (int q = 0; q < kSub; ++q) {
+                            pk[q * kNs] = acc[q].x + acc[q].y;
+                            acc[q] = make_float2(0.f, 0.f);
+                        }
+                    }
+                }
             }
             if constexpr (MODE == 0) {
                 if (ok) {
-                    float* o = sg.out + (long long)(kNs * j + m) * sg.beam_stride + F;
+                    // forms that split items: each output is H0 + H1 (H = the two fine channels
+                    // of a pair added first), split or not; the 2-term form: the running sum
+                    float h1[kSub];
 #pragma unroll
-                    for (int q = 0; q < kSub; ++q) o[(long long)q * sg.sub_stride] = acc[q].x + acc[q].y;
+                    for (int q = 0; q < kSub; ++q) h1[q] = acc[q].x + acc[q].y;
+                    float* o = sg.out + (long long)(kNs * j + m) * sg.beam_stride + F;
+                    if (!SPLIT) {
+#pragma unroll
+                        for (int q = 0; q < kSub; ++q) o[(long long)q * sg.sub_stride] = h1[q];
+                    } else if (half < 0) {
+                        const float* pk = bt.park + (size_t)blockIdx.x * (kSub * kNs) + m;
+                        float h0[kSub];
+#pragma unroll
+                        for (int q = 0; q < kSub; ++q) h0[q] = pk[q * kNs];
+#pragma unroll
+                        for (int q = 0; q < kSub; ++q) o[(long long)q * sg.sub_stride] = h0[q] + h1[q];
+                    } else {
+                        const int slot = item - units.n_full;
+                        float* mine = bt.part + ((size_t)slot * 2 + half) * (kSub * kNs) + m;
+#pragma unroll
+                        for (int q = 0; q < kSub; ++q) mine[q * kNs] = h1[q];
+                        if (second_half(bt.part_tok + (size_t)slot * kNs + m, bt.epoch, half)) {
+                            const float* other = bt.part + ((size_t)slot * 2 + (half ^ 1)) * (kSub * kNs) + m;
+                            float h0[kSub];
+#pragma unroll
+                            for (int q = 0; q < kSub; ++q) h0[q] = __ldcg(other + q * kNs);
+#pragma unroll
+                            for (int q = 0; q < kSub; ++q) o[(long long)q * sg.sub_stride] = h0[q] + h1[q];
+                        }
+                    }
                 }
             }
         }
@@ -540,6 +591,9 @@ __global__ void __launch_bounds__(TcCfg<TERMS>::NT, 1) fused_tc_kernel(const __g
 template <int TERMS, int MODE>
 cudaError_t launch_tc(const Batch& b, int grid, cudaStream_t s) {
     if (b.n_items <= 0) return cudaSuccess;
+    // the detecting 1- and 3-term kernels park and split: they need the plan's buffers
+    if (MODE == 0 && TERMS != 2 && (!b.part || !b.park || !b.part_tok || grid > 2 * kMaxSplit))
+        return cudaErrorInvalidValue;
     const int smem = (int)TcCfg<TERMS>::SMEM;
     cudaError_t e = cudaFuncSetAttribute(fused_tc_kernel<TERMS, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;

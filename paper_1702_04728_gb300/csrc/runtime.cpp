@@ -119,7 +119,9 @@ struct bf_plan_s {
     size_t delays_cap = 0;
     int* d_status = nullptr;
     float* d_part = nullptr;                  // FP32 form: halves of split items (see Batch::part)
-    int* d_part_cnt = nullptr;
+    unsigned long long* d_part_tok = nullptr;
+    float* d_park = nullptr;                  // tensor-core form: per-CTA first halves (see Batch::park)
+    unsigned long long launches = 0;          // launch epochs handed to the kernels
 
     std::mutex mu;
     std::condition_variable cv;
@@ -281,7 +283,8 @@ Batch make_batch(const bf_plan_s* p) {
     b.a_tc_stride = p->terms ? tc_a_bytes(p->terms) : 0;
     b.status = p->d_status;
     b.part = p->d_part;
-    b.part_cnt = p->d_part_cnt;
+    b.part_tok = p->d_part_tok;
+    b.park = p->d_park;
     return b;
 }
 
@@ -424,6 +427,7 @@ int launch_jobs(bf_plan_s* p, std::vector<Job>& jobs, size_t bytes) {
     }
     for (auto& bb : batches) {
         bb.a_tc = p->d_atc;                       // tables may have been created above
+        bb.epoch = ++p->launches;
         cudaError_t e = p->terms ? fused_tc_launch(bb, p->terms, 0, std::min(p->grid, bb.n_items), p->stream)
                                  : fused_fp32_launch(bb, std::min(p->grid, bb.n_items), p->stream);
         if (e != cudaSuccess) return cuda_fail(e, "fused kernel launch");
@@ -654,12 +658,14 @@ int bf_plan(const bf_config* cfg, bf_plan_t* out) {
     CK(cudaHostAlloc(&p->h_status, sizeof(int), cudaHostAllocMapped));
     *p->h_status = 0;
     CK(cudaHostGetDevicePointer(&p->d_status, p->h_status, 0));
-    if (!p->terms && p->grid <= 2 * kMaxSplit) {
-        // a launch splits at most grid / 2 items: two halves of 16 x 256 floats each
+    if (p->grid <= 2 * kMaxSplit) {
+        // a launch splits at most grid / 2 items: two halves of 16 x 256 floats each, and
+        // one token per bin; the tensor-core form also parks each CTA's first half
         const size_t slots = (size_t)p->grid / 2 + 1;
         CK(cudaMalloc(&p->d_part, slots * 2 * kSub * kNs * sizeof(float)));
-        CK(cudaMalloc(&p->d_part_cnt, slots * sizeof(int)));
-        CK(cudaMemset(p->d_part_cnt, 0, slots * sizeof(int)));
+        CK(cudaMalloc(&p->d_part_tok, slots * kNs * sizeof(unsigned long long)));
+        CK(cudaMemset(p->d_part_tok, 0, slots * kNs * sizeof(unsigned long long)));
+        if (p->terms) CK(cudaMalloc(&p->d_park, (size_t)p->grid * kSub * kNs * sizeof(float)));
     }
 
     if (p->cfg.mode == BF_MODE_SERVING) {
@@ -807,7 +813,8 @@ int bf_destroy(bf_plan_t p) {
     cudaFree(p->d_tw512);
     cudaFree(p->d_tw128);
     cudaFree(p->d_part);
-    cudaFree(p->d_part_cnt);
+    cudaFree(p->d_part_tok);
+    cudaFree(p->d_park);
     if (p->d_atc) cudaFree(p->d_atc);
     if (p->d_delays) cudaFree(p->d_delays);
     if (p->h_status) cudaFreeHost(p->h_status);

@@ -167,11 +167,19 @@ def test_node_slice_full_size_sampled(plan):
     assert_rel(got, ref)
 
 
-def test_tail_split_items_match_whole_items(plan):
+@pytest.mark.parametrize("form,rel", [(B.BF_FP32_FFT, REL), (B.BF_TC_DFT256, REL), (B.BF_TC_DFT256_X1, 5e-3),
+                                      (B.BF_TC_DFT256_X2, 1e-3)])
+def test_tail_split_items_match_whole_items(built_lib, form, rel):
     """A launch whose last round of items would leave at least half of the CTAs
-    idle runs each item of that round as two half units on two CTAs.  The output
-    must equal, bit for bit, a run of the same stream in two requests whose
-    items all run whole, and the oracle within tolerance."""
+    idle runs each item of that round as two half units on two CTAs (the 2-term
+    form never splits).  The output must equal, bit for bit, a run of the same
+    stream in two requests whose items all run whole, and the oracle within the
+    form's tolerance."""
+    with B.Plan(form=form) as plan:
+        _tail_split_case(plan, rel)
+
+
+def _tail_split_case(plan, rel):
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     nf1, nf2 = sms // 4, 5
     items = 4 * (nf1 + nf2)
@@ -195,7 +203,7 @@ def test_tail_split_items_match_whole_items(plan):
     rng = np.random.default_rng(33)
     picks = [(0, int(rng.integers(1024)), fr) for fr in range(nf1 - 1, nf1 + nf2) for _ in range(3)]
     ref = O.beamform_sample(raw, [freq], picks)
-    assert_rel(np.stack([got[b, 0:16, fr] for _, b, fr in picks]), ref)
+    assert_rel(np.stack([got[b, 0:16, fr] for _, b, fr in picks]), ref, rel=rel)
 
 
 @pytest.mark.parametrize("form", [B.BF_FP32_FFT, B.BF_TC_DFT256])
