@@ -47,6 +47,7 @@ struct Batch {
     int n_segs;
     int n_items;
     const int16_t* lut;      // [n_tables][256]   clamp table, Eq. (1)
+    const int16_t* order;    // [n_tables][256]   FP32 form: beam taken by consumer slot (TMEM lane + 128 x half)
     const float2* ew;        // [n_tables][4 ew][4 cyl] E-W phases
     const float2* tw512;     // [512] exp(-2 pi i e / 512)
     const float2* tw128;     // [128] exp(-2 pi i e / 128)

@@ -58,7 +58,7 @@ constexpr int kRawB = 2 * kInput;                    // per producer warp and bu
 constexpr size_t kSmemBins = 2 * (size_t)kBinsF4 * 16;   // double-buffered across iterations
 constexpr size_t kSmemYsc = (size_t)kWarps * kYscF4 * 16;
 constexpr size_t kSmemRaw = (size_t)kWarps * kRawB;      // raw rows (cp.async), one iteration ahead
-constexpr size_t kSmemLut = kNs * sizeof(int);
+constexpr size_t kSmemLut = 2 * kNs * sizeof(int);   // bins and beams in gather order
 constexpr size_t kSmemTw = 8 * 8 * 16;               // pair twiddles of the first up-channel pass
 constexpr size_t kSmemPark = (size_t)kSub * kNs * sizeof(float);   // first half of the current item
 constexpr size_t kSmemTotal = kSmemBins + kSmemYsc + kSmemRaw + kSmemLut + kSmemTw + kSmemPark;
@@ -217,6 +217,7 @@ __global__ void __launch_bounds__(kThreads, 1) fused_fp32_kernel(const __grid_co
     float4* ysc_all = reinterpret_cast<float4*>(smem + kSmemBins);
     unsigned char* raw_all = smem + kSmemBins + kSmemYsc;
     int* lut_s = reinterpret_cast<int*>(smem + kSmemBins + kSmemYsc + kSmemRaw);
+    int* beam_s = lut_s + kNs;
     float4* tw_s = reinterpret_cast<float4*>(smem + kSmemBins + kSmemYsc + kSmemRaw + kSmemLut);
     float* park_s = reinterpret_cast<float*>(smem + kSmemBins + kSmemYsc + kSmemRaw + kSmemLut + kSmemTw);
     __shared__ uint32_t tmem_base_s;
@@ -333,7 +334,7 @@ __global__ void __launch_bounds__(kThreads, 1) fused_fp32_kernel(const __grid_co
         const int cq = warp - kWarps;                    // TMEM lane quarter
         const int ctid = tid - 32 * kWarps;
         const uint32_t tlane = tmem + (static_cast<uint32_t>(32 * cq) << 16);
-        const int m0 = 32 * cq + lane;                   // bins m0 (half 0) and m0 + 128 (half 1)
+        const int m0 = 32 * cq + lane;                   // consumer slots m0 (half 0) and m0 + 128 (half 1)
         uint32_t g = 0;
         for (int un = blockIdx.x; un < units.n_units; un += gridDim.x) {
             int item, ps0, ps1, half;
@@ -344,12 +345,17 @@ __global__ void __launch_bounds__(kThreads, 1) fused_fp32_kernel(const __grid_co
             const int local = item - sg.item_begin;
             const int F = local >> 2, j = local & 3;
             bar_sync_n(kBarCons, 32 * kCons);             // the previous item's table reads are done
-            for (int i = ctid; i < kNs; i += 32 * kCons) lut_s[i] = bt.lut[sg.table * kNs + i];
+            // consumer slot i (TMEM lane + 128 x half) takes beam order[i]
+            for (int i = ctid; i < kNs; i += 32 * kCons) {
+                const int bm = bt.order[sg.table * kNs + i];
+                beam_s[i] = bm;
+                lut_s[i] = bt.lut[sg.table * kNs + bm];
+            }
             bar_sync_n(kBarCons, 32 * kCons);
             const int Lsw0 = bsw(lut_s[m0]), Lsw1 = bsw(lut_s[m0 + 128]);
-            // output addresses are formed where they are used (registers are tight here)
-            auto out0 = [&] { return sg.out + (long long)(kNs * j + m0) * sg.beam_stride + F; };
-            auto out1 = [&] { return sg.out + (long long)(kNs * j + m0 + 128) * sg.beam_stride + F; };
+            // the slots' beams (gather order); output addresses are formed where they are used
+            auto out0 = [&] { return sg.out + (long long)(kNs * j + beam_s[m0]) * sg.beam_stride + F; };
+            auto out1 = [&] { return sg.out + (long long)(kNs * j + beam_s[m0 + 128]) * sg.beam_stride + F; };
             float acc0[kSub], acc1[kSub];
 #pragma unroll
             for (int s2 = 0; s2 < kSub; ++s2) {
@@ -388,8 +394,8 @@ __global__ void __launch_bounds__(kThreads, 1) fused_fp32_kernel(const __grid_co
                 tmem_wait_st();
                 // second pass: 16-point DFT over b for fine channels q = c + 8 d (this warp's lanes only)
                 const long long dbase = ((((long long)(F * kTds + blk) * kPol + pol) * kEw + j) * kNs) * kUp;
-                upchan_pass2(tlane, 0, acc0, kDump ? bt.dump + dbase + (long long)m0 * kUp : nullptr);
-                upchan_pass2(tlane, 1, acc1, kDump ? bt.dump + dbase + (long long)(m0 + 128) * kUp : nullptr);
+                upchan_pass2(tlane, 0, acc0, kDump ? bt.dump + dbase + (long long)beam_s[m0] * kUp : nullptr);
+                upchan_pass2(tlane, 1, acc1, kDump ? bt.dump + dbase + (long long)beam_s[m0 + 128] * kUp : nullptr);
                 // the next pass's gathers overwrite these TMEM columns in this warp's program order
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
                 if constexpr (!kDump) {
@@ -425,7 +431,7 @@ __global__ void __launch_bounds__(kThreads, 1) fused_fp32_kernel(const __grid_co
                     for (int s2 = 0; s2 < kSub; ++s2) o[(long long)s2 * sg.sub_stride] = h[s2] + acc1[s2];
                 } else {
                     // half unit: publish this half; the second of the two halves to finish
-                    // adds them (per thread: bins m0 and m0 + 128)
+                    // adds them (per thread: slots m0 and m0 + 128)
                     const int slot = item - units.n_full;
                     float* mine = bt.part + ((size_t)slot * 2 + half) * (kSub * kNs);
 #pragma unroll

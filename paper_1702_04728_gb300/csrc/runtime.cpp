@@ -108,6 +108,7 @@ struct bf_plan_s {
     bool own_stream = false;
 
     int16_t* d_lut = nullptr;
+    int16_t* d_order = nullptr;               // FP32 form: gather order of the beams per table
     float2* d_ew = nullptr;
     float2* d_tw512 = nullptr;
     float2* d_tw128 = nullptr;
@@ -243,6 +244,61 @@ uint64_t freq_key(double f) {
 }
 
 // Index of the device table row for frequency f (uploaded on first use).
+// Order in which the FP32 kernel's consumer threads take the 256 N-S beams:
+// thread (TMEM lane ell, bin half hh) handles beam order[ell + 128 hh].  A warp
+// gathers its 32 beams' bins from one shared-memory row with one 16-byte load
+// per lane, eight consecutive lanes at a time; eight beams whose bins fall in
+// distinct 16-byte bank groups (or that share a bin) load without a bank
+// conflict, while the beams' natural order puts several bins of a group into
+// one load.  Any order gives the same result; this one packs, per group of
+// eight slots, beams of distinct bank groups (first fit, largest bin first).
+void gather_order(const int32_t* lut, int16_t* order) {
+    std::map<int, std::vector<int>> by_bin;
+    for (int m = 0; m < kNs; ++m) by_bin[lut[m]].push_back(m);
+    struct Unit {
+        int group;
+        std::vector<int> beams;
+    };
+    std::vector<Unit> units;
+    for (auto& kv : by_bin) {
+        const int L = kv.first, sw = L ^ ((L >> 3) & 1);     // the kernel's bin swizzle
+        for (size_t i = 0; i < kv.second.size(); i += 8) {
+            Unit u;
+            u.group = sw & 7;
+            u.beams.assign(kv.second.begin() + i, kv.second.begin() + std::min(kv.second.size(), i + 8));
+            units.push_back(std::move(u));
+        }
+    }
+    std::stable_sort(units.begin(), units.end(),
+                     [](const Unit& a, const Unit& b) { return a.beams.size() > b.beams.size(); });
+    constexpr int kOct = kNs / 8;
+    std::vector<int> members[kOct];
+    unsigned used[kOct] = {};
+    for (const Unit& u : units) {
+        const int n = (int)u.beams.size();
+        int o = 0;
+        while (o < kOct && ((int)members[o].size() + n > 8 || ((used[o] >> u.group) & 1))) ++o;
+        if (o == kOct) {                                   // no conflict-free place: any with room
+            o = 0;
+            while (o < kOct && (int)members[o].size() + n > 8) ++o;
+        }
+        if (o < kOct) {
+            members[o].insert(members[o].end(), u.beams.begin(), u.beams.end());
+            used[o] |= 1u << u.group;
+            continue;
+        }
+        for (int m : u.beams) {                            // split over whatever room is left
+            int q = 0;
+            while (members[q].size() == 8) ++q;
+            members[q].push_back(m);
+            used[q] |= 1u << u.group;
+        }
+    }
+    int k = 0;
+    for (int o = 0; o < kOct; ++o)
+        for (int m : members[o]) order[k++] = (int16_t)m;
+}
+
 int table_for(bf_plan_s* p, double f, int* idx) {
     auto it = p->table_of_freq.find(freq_key(f));
     if (it != p->table_of_freq.end()) {
@@ -258,6 +314,9 @@ int table_for(bf_plan_s* p, double f, int* idx) {
     for (int m = 0; m < kNs; ++m) lut16[m] = (int16_t)lut[m];
     ew_table(p, f, ew);
     CK(cudaMemcpy(p->d_lut + (size_t)n * kNs, lut16, sizeof lut16, cudaMemcpyHostToDevice));
+    int16_t order[kNs];
+    gather_order(lut, order);
+    CK(cudaMemcpy(p->d_order + (size_t)n * kNs, order, sizeof order, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(p->d_ew + (size_t)n * kEw * kCyl, ew, sizeof ew, cudaMemcpyHostToDevice));
     if (p->terms) {
         if (n >= kTcTableCap) return fail(BF_ENOMEM, "too many distinct channel frequencies for the tensor-core form");
@@ -276,6 +335,7 @@ Batch make_batch(const bf_plan_s* p) {
     Batch b;
     std::memset(&b, 0, sizeof b);
     b.lut = p->d_lut;
+    b.order = p->d_order;
     b.ew = p->d_ew;
     b.tw512 = p->d_tw512;
     b.tw128 = p->d_tw128;
@@ -645,6 +705,7 @@ int bf_plan(const bf_config* cfg, bf_plan_t* out) {
         p->own_stream = true;
     }
     CK(cudaMalloc(&p->d_lut, (size_t)kTableCap * kNs * sizeof(int16_t)));
+    CK(cudaMalloc(&p->d_order, (size_t)kTableCap * kNs * sizeof(int16_t)));
     CK(cudaMalloc(&p->d_ew, (size_t)kTableCap * kEw * kCyl * sizeof(float2)));
     CK(cudaMalloc(&p->d_tw512, kBins * sizeof(float2)));
     CK(cudaMalloc(&p->d_tw128, kUp * sizeof(float2)));
@@ -809,6 +870,7 @@ int bf_destroy(bf_plan_t p) {
         for (auto ev : p->event_pool) cudaEventDestroy(ev);
     }
     cudaFree(p->d_lut);
+    cudaFree(p->d_order);
     cudaFree(p->d_ew);
     cudaFree(p->d_tw512);
     cudaFree(p->d_tw128);
