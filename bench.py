@@ -36,7 +36,6 @@ FLOP_PER_SAMPLE = 162.0          # conventional 5 N log2 N FFT count + E-W + det
 BYTES_PER_SAMPLE = 1.0 + 1024 * 16 * 4 / (384 * 2048)   # 1 B in + float32 out
 
 
-E2E_SPLIT = 4          # requests per channel in the end-to-end measurement
 
 KERNEL_SOURCES = {
     "fused_fp32_kernel": ["fused_fp32.cu", "device_common.cuh", "bf_internal.h"],
@@ -440,38 +439,49 @@ def main():
         form_outs[fname] = fo[:, :, :16].cpu().numpy()
 
     # end to end through the public API: pinned host in -> device -> beamform -> host out.
-    # One request per channel; the copy of channel c+1 overlaps the beamforming of c, and
-    # channels alternate between two plans on two streams so that the CTAs of the next
-    # channel fill the SMs a channel's last wave leaves idle (512 work items = 3.4 waves).
+    # Each channel goes in requests of whole frames on one stream (the plan's carry state joins
+    # them).  A request holds one wave of work items (SMs / 4 E-W beams frames), so no launch
+    # ends with a partial wave; the remainder makes a short first piece for the first channel
+    # (its copy cannot overlap anything) and a short last piece for the others (the last one's
+    # compute is the exposed tail, and it splits into half items).  Channels alternate between
+    # two plans on two streams; the copy of piece i + 1 is issued before piece i's request, so
+    # the copy engine never waits for the host.
     copy_s, d2h_s = torch.cuda.Stream(), torch.cuda.Stream()
     stream2 = torch.cuda.Stream()
     plan2 = B.Plan(stream=stream2, form=headline_form)
     e2e_plans = [(plan, stream), (plan2, stream2)]
-    # each channel goes in E2E_SPLIT requests of whole frames on one stream (the plan's carry
-    # state joins them), so the compute of the last piece, the exposed tail, is short
-    split = E2E_SPLIT
-    piece = (N_SAMP // split) // 384 * 384
-    bounds = [(k * piece, N_SAMP if k == split - 1 else (k + 1) * piece) for k in range(split)]
-    pieces = [(c, k) for c in range(N_CHAN) for k in range(split)]
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    wave = max(1, n_sm // 4)
+    nfc = N_SAMP // 384
+    full, rest = divmod(nfc, wave)
+    sched = [([rest] if rest else []) + [wave] * full] + [[wave] * full + ([rest] if rest else [])] * (N_CHAN - 1)
+    pieces = []
+    for c in range(N_CHAN):
+        lo = 0
+        for k, nfr in enumerate(sched[c]):
+            pieces.append((c, k, lo, lo + 384 * nfr, k == len(sched[c]) - 1))
+            lo += 384 * nfr
     outs_p = {(c, k): torch.empty(1024, 16, (hi - lo) // 384, dtype=torch.float32, device="cuda")
-              for c in range(N_CHAN) for k, (lo, hi) in enumerate(bounds)}
-    host_outs_p = {p_: torch.empty(tuple(outs_p[p_].shape), dtype=torch.float32).pin_memory() for p_ in pieces}
-    in_ev = {p_: torch.cuda.Event() for p_ in pieces}
-    done_ev = {p_: torch.cuda.Event() for p_ in pieces}
+              for c, k, lo, hi, _ in pieces}
+    host_outs_p = {p_: torch.empty(tuple(v.shape), dtype=torch.float32).pin_memory() for p_, v in outs_p.items()}
+    in_ev = {p_[:2]: torch.cuda.Event() for p_ in pieces}
+    done_ev = {p_[:2]: torch.cuda.Event() for p_ in pieces}
 
     def e2e_step():
-        with torch.cuda.stream(copy_s):                 # all host->device copies back to back
-            for c, k in pieces:
-                lo, hi = bounds[k]
+        def h2d(i):
+            c, k, lo, hi, _ = pieces[i]
+            with torch.cuda.stream(copy_s):
                 vin[c, lo:hi].copy_(host_in[c, lo:hi], non_blocking=True)
                 in_ev[(c, k)].record(copy_s)
+        h2d(0)
         tk = []
-        for c, k in pieces:                             # beamform each piece once it has landed
-            lo, hi = bounds[k]
+        for i, (c, k, lo, hi, last) in enumerate(pieces):
+            if i + 1 < len(pieces):
+                h2d(i + 1)
             pl, st = e2e_plans[c % 2]
-            st.wait_event(in_ev[(c, k)])
+            st.wait_event(in_ev[(c, k)])                # beamform the piece once it has landed
             _, t = pl.submit(vin[c:c + 1, lo:hi], freqs[c:c + 1], outs_p[(c, k)], stream_id=100 + c,
-                             flags=B.BF_END_OF_STREAM if k == split - 1 else 0, n_samples=hi - lo)
+                             flags=B.BF_END_OF_STREAM if last else 0, n_samples=hi - lo)
             done_ev[(c, k)].record(st)
             tk.append((pl, t))
             with torch.cuda.stream(d2h_s):              # device->host of each output as it is done
@@ -488,8 +498,8 @@ def main():
         e2e_step()
     barrier()
     e2e_ms = (time.perf_counter() - t0) * 1e3 / args.e2e_steps
-    host_out = torch.cat([torch.cat([host_outs_p[(c, k)] for k in range(split)], dim=2) for c in range(N_CHAN)],
-                         dim=1)
+    host_out = torch.cat([torch.cat([host_outs_p[(c, k)] for k in range(len(sched[c]))], dim=2)
+                          for c in range(N_CHAN)], dim=1)
 
     ms_t = torch.tensor([ms, e2e_ms], device="cuda")
     if ws > 1:
@@ -530,10 +540,11 @@ def main():
             "roofline": roof,
             "e2e": {"value": samples * ws / (e2e_ms * 1e-3), "unit": "input-samples/s",
                     "h2d_bytes_per_step": samples, "d2h_bytes_per_step": out.numel() * 4,
-                    "ms_per_step": e2e_ms, "how": f"wall clock; {E2E_SPLIT} requests per channel on one "
-                                                  "stream, H2D of the next piece overlapping beamforming of "
-                                                  "the previous one, channels alternating between two plans "
-                                                  "on two streams, D2H of each output"},
+                    "ms_per_step": e2e_ms, "how": f"wall clock; requests of {wave} frames (one wave of "
+                                                  "work items) per channel on one stream, a short first and "
+                                                  "last piece, H2D of the next piece overlapping beamforming "
+                                                  "of the previous one, channels alternating between two "
+                                                  "plans on two streams, D2H of each output"},
             "gpu_launches": args.steps,
             "forms": form_runs,
             "post": post,

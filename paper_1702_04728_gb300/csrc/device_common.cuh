@@ -256,9 +256,9 @@ __device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
 }
 
 // Work units.  A unit is an item (F, j) with all six passes, or one half of an
-// item: passes 0-2 or 3-5.  When the last round of items would leave at least
-// half of the CTAs idle, each item of that round becomes two half units on two
-// CTAs; the second to finish adds the two halves.  Every output is the sum of
+// item: passes 0-2 or 3-5.  When the last (or only) round of items would leave
+// at least half of the CTAs idle, each item of that round becomes two half
+// units on two CTAs; the second to finish adds the two halves.  Every output is the sum of
 // the two halves (H0 + H1, one addition), whether or not its item was split,
 // so the result does not depend on how a request was batched.
 struct Units {
@@ -267,7 +267,7 @@ struct Units {
 };
 __device__ __forceinline__ Units make_units(int n_items, int grid, bool can_split) {
     Units u{n_items, n_items};
-    if (can_split && n_items > grid) {
+    if (can_split) {
         const int rem = n_items % grid;
         if (rem > 0 && 2 * rem <= grid) {
             u.n_full = n_items - rem;

@@ -488,8 +488,12 @@ int launch_jobs(bf_plan_s* p, std::vector<Job>& jobs, size_t bytes) {
     for (auto& bb : batches) {
         bb.a_tc = p->d_atc;                       // tables may have been created above
         bb.epoch = ++p->launches;
-        cudaError_t e = p->terms ? fused_tc_launch(bb, p->terms, 0, std::min(p->grid, bb.n_items), p->stream)
-                                 : fused_fp32_launch(bb, std::min(p->grid, bb.n_items), p->stream);
+        // a launch of at most half a grid of items runs every item as two halves on two CTAs
+        // (the 2-term tensor-core form never splits)
+        int grid = std::min(p->grid, bb.n_items);
+        if (p->terms != 2 && 2 * bb.n_items <= p->grid) grid = 2 * bb.n_items;
+        cudaError_t e = p->terms ? fused_tc_launch(bb, p->terms, 0, grid, p->stream)
+                                 : fused_fp32_launch(bb, grid, p->stream);
         if (e != cudaSuccess) return cuda_fail(e, "fused kernel launch");
     }
     for (auto& c : carries) {
