@@ -141,6 +141,9 @@ int bf_frames_out(bf_plan_t p, uint64_t stream_id, int64_t n_samples, int64_t* n
  * was admitted at once, BF_EQUEUED if it waits for memory); the plan thread
  * batches admitted requests of different streams into one launch.  *ticket
  * identifies the request for bf_poll.  Requests of one stream run in order.
+ * Results do not depend on batching: a stream cut into requests anywhere, or
+ * run alone or in a mixed batch, gives the same output bits (every sum runs
+ * in a fixed order, whichever CTAs take its parts).
  */
 int bf_submit(bf_plan_t p, const bf_request* r, uint64_t* ticket);
 
