@@ -76,40 +76,83 @@ __device__ __forceinline__ void dft4(cp& a0, cp& a1, cp& a2, cp& a3) {
     a3 = csub(d02, d13);
 }
 
-// forward DFT8 (2 x 4), natural order in and out
+// Radix-2 butterfly with a twiddle, factored for fused multiply-adds: with
+// w = c (1 + i t), (a, b) -> (a + w b, a - w b) as p = (1 + i t) b (two FMA)
+// and a +- c p (four FMA), six operations instead of a complex product and two
+// complex additions (eight).  E = e in units of 2 pi / 16, w = exp(-2 pi i E / 16);
+// c = cos(2 pi E / 16), t = -tan(2 pi E / 16), rounded from double precision.
+template <int E>
+__device__ __forceinline__ void bfly_tw(cp& a, cp& b) {
+    constexpr float kc[8] = {1.f, 9.238795325e-01f, 7.071067812e-01f, 3.826834324e-01f,
+                             0.f, -3.826834324e-01f, -7.071067812e-01f, -9.238795325e-01f};
+    constexpr float kt[8] = {0.f, -4.142135624e-01f, -1.0f, -2.414213562e+00f,
+                             0.f, 2.414213562e+00f, 1.0f, 4.142135624e-01f};
+    if constexpr (E == 0) {
+        const cp y = cadd(a, b), z = csub(a, b);
+        a = y;
+        b = z;
+    } else if constexpr (E == 4) {
+        // w = -i: a - i b = (a.re + b.im, a.im - b.re)
+        const cp y = {add2(a.re, b.im), sub2(a.im, b.re)};
+        const cp z = {sub2(a.re, b.im), add2(a.im, b.re)};
+        a = y;
+        b = z;
+    } else {
+        const float c = kc[E], t = kt[E];
+        const float2 pre = fma2(b.im, bc(-t), b.re), pim = fma2(b.re, bc(t), b.im);
+        const cp y = {fma2(pre, bc(c), a.re), fma2(pim, bc(c), a.im)};
+        const cp z = {fma2(pre, bc(-c), a.re), fma2(pim, bc(-c), a.im)};
+        a = y;
+        b = z;
+    }
+}
+
+// forward DFT8 (2 x 4), natural order in and out; the last stage's twiddles
+// W8^k = W16^{2k} fused into its butterflies
 __device__ __forceinline__ void dft8(cp (&x)[8]) {
     dft4(x[0], x[2], x[4], x[6]);
     dft4(x[1], x[3], x[5], x[7]);
-    x[3] = twiddle<8>(x[3], 1);
-    x[5] = twiddle<8>(x[5], 2);
-    x[7] = twiddle<8>(x[7], 3);
+    bfly_tw<0>(x[0], x[1]);
+    bfly_tw<2>(x[2], x[3]);
+    bfly_tw<4>(x[4], x[5]);
+    bfly_tw<6>(x[6], x[7]);
+    // X[k] = x[2k], X[k + 4] = x[2k + 1]
     cp y[8];
 #pragma unroll
     for (int k1 = 0; k1 < 4; ++k1) {
-        y[k1] = cadd(x[2 * k1], x[2 * k1 + 1]);
-        y[k1 + 4] = csub(x[2 * k1], x[2 * k1 + 1]);
+        y[k1] = x[2 * k1];
+        y[k1 + 4] = x[2 * k1 + 1];
     }
 #pragma unroll
     for (int k = 0; k < 8; ++k) x[k] = y[k];
+}
+
+// second-stage group k1 of dft16: the four inputs x[4 k1 + n2] with their
+// twiddles W16^{n2 k1} folded into three factored radix-2 levels
+template <int K1>
+__device__ __forceinline__ void dft16_group(cp& x0, cp& x1, cp& x2, cp& x3) {
+    bfly_tw<(2 * K1) & 15>(x0, x2);          // x0 + w2 x2, x0 - w2 x2
+    bfly_tw<(2 * K1) & 15>(x1, x3);          // u = x1 + w2 x3, v = x1 - w2 x3
+    bfly_tw<K1>(x0, x1);                     // out0 = s + w1 u, out2 = s - w1 u
+    bfly_tw<(K1 + 4) & 15>(x2, x3);          // out1 = d - i w1 v, out3 = d + i w1 v
 }
 
 // forward DFT16 (4 x 4), natural order in and out
 __device__ __forceinline__ void dft16(cp (&x)[16]) {
 #pragma unroll
     for (int n2 = 0; n2 < 4; ++n2) dft4(x[n2], x[4 + n2], x[8 + n2], x[12 + n2]);
-#pragma unroll
-    for (int n2 = 1; n2 < 4; ++n2)
-#pragma unroll
-        for (int k1 = 1; k1 < 4; ++k1) x[4 * k1 + n2] = twiddle<16>(x[4 * k1 + n2], n2 * k1);
+    dft16_group<0>(x[0], x[1], x[2], x[3]);
+    dft16_group<1>(x[4], x[5], x[6], x[7]);
+    dft16_group<2>(x[8], x[9], x[10], x[11]);
+    dft16_group<3>(x[12], x[13], x[14], x[15]);
+    // group k1 holds (out0, out2, out1, out3) in its slots (0, 1, 2, 3); X[k1 + 4 k2] = out_k2
     cp y[16];
 #pragma unroll
     for (int k1 = 0; k1 < 4; ++k1) {
-        cp a0 = x[4 * k1], a1 = x[4 * k1 + 1], a2 = x[4 * k1 + 2], a3 = x[4 * k1 + 3];
-        dft4(a0, a1, a2, a3);
-        y[k1] = a0;
-        y[k1 + 4] = a1;
-        y[k1 + 8] = a2;
-        y[k1 + 12] = a3;
+        y[k1] = x[4 * k1];
+        y[k1 + 8] = x[4 * k1 + 1];
+        y[k1 + 4] = x[4 * k1 + 2];
+        y[k1 + 12] = x[4 * k1 + 3];
     }
 #pragma unroll
     for (int k = 0; k < 16; ++k) x[k] = y[k];
