@@ -47,49 +47,88 @@ __global__ void __launch_bounds__(kMapThreads) skymap_kernel(const float* __rest
 // 255).  FP32, sums frame by frame, every operation rounded once (the _rn
 // intrinsics keep the compiler from fusing multiply and add), so the codes
 // follow a fixed evaluation order.  A CTA stages its 32 rows through shared
-// memory with coalesced loads; rows longer than the stage are read directly.
+// memory with coalesced loads; when the row length is a multiple of 4 (and the
+// code array 4-byte aligned) the codes
+// go back through shared memory as 32-bit words (rows padded by one word, no
+// bank conflicts) and leave with coalesced stores, row by row.  Rows longer
+// than the stage are read and written directly.
 constexpr int kU8Rows = 32;
 constexpr int kU8Stage = 256;          // frames staged per row
+constexpr int kU8Words = kU8Stage / 4 + 1;
 
 __global__ void __launch_bounds__(kU8Rows) rescale_u8_kernel(const float* __restrict__ in, long long rows,
                                                                long long nf, uint8_t* __restrict__ codes,
                                                                float* __restrict__ stats) {
     __shared__ float st[kU8Rows][kU8Stage + 1];
+    __shared__ uint32_t cw[kU8Rows][kU8Words];
     const long long r0 = (long long)blockIdx.x * kU8Rows;
     const long long r = r0 + threadIdx.x;
     const bool staged = nf <= kU8Stage;
+    const bool words = staged && (nf & 3) == 0 && (reinterpret_cast<uintptr_t>(codes) & 3) == 0;
+    const int nr = (int)min((long long)kU8Rows, rows - r0);
     if (staged) {
-        const int nr = (int)min((long long)kU8Rows, rows - r0);
-        for (int rr = 0; rr < nr; ++rr)
-            for (long long f = threadIdx.x; f < nf; f += kU8Rows) st[rr][f] = __ldg(in + (r0 + rr) * nf + f);
+        // the CTA's rows are contiguous: walk the block with 32 consecutive floats per load
+        // instruction, many loads in flight (the row and column advance without a division)
+        const float* src = in + r0 * nf;
+        const long long n = (long long)nr * nf;
+        int rr = (int)(threadIdx.x / nf);
+        long long f = threadIdx.x - rr * nf;
+        const long long step_r = kU8Rows / nf, step_f = kU8Rows % nf;
+#pragma unroll 16
+        for (long long i = threadIdx.x; i < n; i += kU8Rows) {
+            st[rr][f] = __ldg(src + i);
+            rr += (int)step_r;
+            f += step_f;
+            if (f >= nf) {
+                f -= nf;
+                ++rr;
+            }
+        }
         __syncthreads();
     }
-    if (r >= rows) return;
-    const float* x = in + r * nf;
-    auto val = [&](long long f) -> float { return staged ? st[threadIdx.x][f] : __ldg(x + f); };
-    float s = 0.f;
-    for (long long f = 0; f < nf; ++f) s = __fadd_rn(s, val(f));
-    const float mean = __fdiv_rn(s, (float)nf);
-    float q = 0.f;
-    for (long long f = 0; f < nf; ++f) {
-        const float d = __fsub_rn(val(f), mean);
-        q = __fadd_rn(q, __fmul_rn(d, d));
-    }
-    const float sd = __fsqrt_rn(__fdiv_rn(q, (float)nf));
-    if (stats) {
-        stats[2 * r] = mean;
-        stats[2 * r + 1] = sd;
-    }
-    const float inv = sd > 0.f ? __fdiv_rn(1.f, sd) : 0.f;
-    uint8_t* c = codes + r * nf;
-    for (long long f = 0; f < nf; ++f) {
-        float v = 64.f;
-        if (sd > 0.f) {
-            const float z = __fmul_rn(__fsub_rn(val(f), mean), inv);
-            v = floorf(__fadd_rn(__fadd_rn(64.f, __fmul_rn(16.f, z)), 0.5f));
+    if (r < rows) {
+        const float* x = in + r * nf;
+        auto val = [&](long long f) -> float { return staged ? st[threadIdx.x][f] : __ldg(x + f); };
+        float s = 0.f;
+        for (long long f = 0; f < nf; ++f) s = __fadd_rn(s, val(f));
+        const float mean = __fdiv_rn(s, (float)nf);
+        float q = 0.f;
+        for (long long f = 0; f < nf; ++f) {
+            const float d = __fsub_rn(val(f), mean);
+            q = __fadd_rn(q, __fmul_rn(d, d));
         }
-        v = v < 0.f ? 0.f : (v > 255.f ? 255.f : v);
-        c[f] = (uint8_t)v;
+        const float sd = __fsqrt_rn(__fdiv_rn(q, (float)nf));
+        if (stats) {
+            stats[2 * r] = mean;
+            stats[2 * r + 1] = sd;
+        }
+        const float inv = sd > 0.f ? __fdiv_rn(1.f, sd) : 0.f;
+        auto code = [&](long long f) -> uint32_t {
+            float v = 64.f;
+            if (sd > 0.f) {
+                const float z = __fmul_rn(__fsub_rn(val(f), mean), inv);
+                v = floorf(__fadd_rn(__fadd_rn(64.f, __fmul_rn(16.f, z)), 0.5f));
+            }
+            v = v < 0.f ? 0.f : (v > 255.f ? 255.f : v);
+            return (uint32_t)v;
+        };
+        if (words) {
+            for (int w = 0; w < (int)(nf >> 2); ++w)
+                cw[threadIdx.x][w] = code(4 * w) | code(4 * w + 1) << 8 | code(4 * w + 2) << 16 |
+                                     code(4 * w + 3) << 24;
+        } else {
+            uint8_t* c = codes + r * nf;
+            for (long long f = 0; f < nf; ++f) c[f] = (uint8_t)code(f);
+        }
+    }
+    if (words) {
+        __syncthreads();
+        // row r0 + rr starts at a 4-byte boundary of `codes` (nf is a multiple of 4)
+        const int nw = (int)(nf >> 2);
+        for (int rr = 0; rr < nr; ++rr) {
+            uint32_t* dst = reinterpret_cast<uint32_t*>(codes + (r0 + rr) * nf);
+            for (int w = threadIdx.x; w < nw; w += kU8Rows) dst[w] = cw[rr][w];
+        }
     }
 }
 

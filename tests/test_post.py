@@ -59,6 +59,25 @@ def test_rescale_u8_bit_exact():
     assert c[:, :, 17].max() >= 64 + 16 * 6 and c[:, :, 16].max() < 64 + 16 * 6
 
 
+@pytest.mark.parametrize("nf,offset", [(128, 0), (300, 0), (41, 0), (128, 1)])
+def test_rescale_u8_row_lengths_and_alignment(built_lib, nf, offset):
+    """Row lengths that take the staged word path (128), the direct path (300 >
+    256 frames staged), the staged byte path (41, not a multiple of 4), and an
+    output one byte off a 4-byte boundary: codes bit-exact with the oracle."""
+    rng = np.random.default_rng(nf + offset)
+    rows = 77
+    x = torch.from_numpy(rng.gamma(4.0, 1e5, size=(rows, nf)).astype(np.float32)).cuda()
+    buf = torch.zeros(rows * nf + 8, dtype=torch.uint8, device="cuda")
+    codes = buf[offset:offset + rows * nf]
+    stats = torch.empty(rows, 2, dtype=torch.float32, device="cuda")
+    with B.Plan() as p:
+        B.bf_rescale_u8(p.handle, x, rows, nf, codes, stats)
+        torch.cuda.synchronize()
+    ref_codes, ref_stats = O.rescale_u8(x.cpu().numpy().reshape(rows, 1, nf))
+    assert np.array_equal(codes.cpu().numpy().reshape(rows, nf), ref_codes.reshape(rows, nf))
+    assert np.array_equal(stats.cpu().numpy(), ref_stats.reshape(rows, 2))
+
+
 def test_dedisperse_matches_oracle_and_recovers_a_burst(built_lib):
     freqs = [600e6 + 390625.0 * k for k in range(8)]
     dm, T = 150.0, 384 * 64
