@@ -227,6 +227,15 @@ int bf_rescale_u8(bf_plan_t p, const float* d_out, int64_t n_rows, int64_t n_fra
  * be NULL. */
 int bf_debug_tables(const bf_config* cfg, double freq_hz, int32_t* lut_out, float* ew_out);
 
+/* Host-only: the order in which the FP32 form's consumer threads take the 256
+ * N-S beams for one frequency: order_out[ell + 128 h] (int16, host, 256
+ * entries, caller-owned) is the beam of TMEM lane ell, bin half h.  A
+ * permutation of 0..255 chosen so that each group of eight consecutive
+ * slots gathers bins from distinct 16-byte shared-memory bank groups (or
+ * shares a bin); no paper counterpart (an implementation detail exposed for
+ * tests).  BF_EINVAL on a null argument or a non-positive frequency. */
+int bf_debug_gather_order(const bf_config* cfg, double freq_hz, int16_t* order_out);
+
 /* Tensor-core forms only: the GEMM output (N-S beams after E-W phasing) as
  * float2 [block][pol][ew][ns][t], t = 0..127, for n_samples a multiple of 384. */
 int bf_debug_gemm(bf_plan_t p, double freq_hz, const uint8_t* d_vin, int64_t n_samples, float* d_out);

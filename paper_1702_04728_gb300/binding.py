@@ -23,7 +23,7 @@ BF_END_OF_STREAM = 1
 N_BEAMS, N_SUB, FRAME, N_INPUT = 1024, 16, 384, 2048
 
 SYMBOLS = ["bf_config_default", "bf_plan", "bf_frames_out", "bf_submit", "bf_poll", "bf_destroy",
-           "bf_last_error", "bf_skymap", "bf_rescale_u8", "bf_dedisperse", "bf_debug_tables", "bf_debug_gemm", "bf_debug_unpack", "bf_debug_beams",
+           "bf_last_error", "bf_skymap", "bf_rescale_u8", "bf_dedisperse", "bf_debug_tables", "bf_debug_gather_order", "bf_debug_gemm", "bf_debug_unpack", "bf_debug_beams",
            "bf_debug_upchan", "bf_debug_stall", "bf_dedisperse_static"]
 
 
@@ -71,6 +71,7 @@ def lib() -> ctypes.CDLL:
         L.bf_destroy.argtypes = [P]
         L.bf_last_error.argtypes = []
         L.bf_last_error.restype = ctypes.c_char_p
+        L.bf_debug_gather_order.argtypes = [ctypes.POINTER(bf_config), D, ctypes.POINTER(ctypes.c_int16)]
         L.bf_debug_tables.argtypes = [ctypes.POINTER(bf_config), D, ctypes.POINTER(ctypes.c_int32),
                                       ctypes.POINTER(ctypes.c_float)]
         L.bf_debug_unpack.argtypes = [P, P, P, I64]
@@ -180,6 +181,15 @@ def bf_poll(plan: int, ticket: int, timeout_us: int = -1):
 
 def bf_destroy(plan: int) -> None:
     _check(lib().bf_destroy(plan))
+
+
+def bf_debug_gather_order(freq_hz: float, cfg: Optional[bf_config] = None):
+    """Beam taken by each consumer slot (TMEM lane + 128 x bin half) of the FP32 form."""
+    import numpy as np
+    cfg = cfg or bf_config_default()
+    order = (ctypes.c_int16 * 256)()
+    _check(lib().bf_debug_gather_order(ctypes.byref(cfg), float(freq_hz), order))
+    return np.frombuffer(order, dtype=np.int16).copy()
 
 
 def bf_debug_tables(freq_hz: float, cfg: Optional[bf_config] = None):

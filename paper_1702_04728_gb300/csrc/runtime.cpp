@@ -1004,6 +1004,20 @@ int bf_debug_tables(const bf_config* cfg, double freq_hz, int32_t* lut_out, floa
     return BF_OK;
 }
 
+int bf_debug_gather_order(const bf_config* cfg, double freq_hz, int16_t* order_out) {
+    if (!cfg || !order_out || !(freq_hz > 0) || !std::isfinite(freq_hz)) return fail(BF_EINVAL, "bad argument");
+    bf_plan_s tmp;
+    tmp.cfg = *cfg;
+    tmp.ns_sin.resize(kNs);
+    tmp.ew_sin.resize(kEw);
+    int rc = fill_pointings(&tmp, cfg);
+    if (rc) return rc;
+    int32_t lut[kNs];
+    clamp_table(&tmp, freq_hz, lut);
+    gather_order(lut, order_out);
+    return BF_OK;
+}
+
 int bf_debug_unpack(bf_plan_t p, const uint8_t* d_in, float* d_out, int64_t n) {
     if (!p || n < 0 || (n > 0 && (!d_in || !d_out))) return fail(BF_EINVAL, "bad argument");
     CK(cudaSetDevice(p->device));

@@ -84,3 +84,28 @@ def test_plan_without_gpu_reports_cuda_error(built_lib):
     rc = built_lib.bf_plan(ctypes.byref(c), ctypes.byref(h))
     assert rc == B.BF_ECUDA and h.value is None
     assert B.bf_last_error()
+
+
+@pytest.mark.parametrize("freq", [410e6, 520e6, 600e6, 650e6, 700e6, 790e6, 799.8e6])
+def test_gather_order_is_a_conflict_avoiding_permutation(built_lib, freq):
+    """The FP32 form's consumer slots take the beams in a per-frequency order: a
+    permutation of the 256 beams (each output is written once) in which eight
+    consecutive slots, gathered by one 16-byte load phase, mostly hit distinct
+    bank groups of the swizzled bin row (bsw(L) mod 8) or share a bin."""
+    order = B.bf_debug_gather_order(freq).astype(int)
+    assert sorted(order) == list(range(256))
+    lut = O.clamp_lut(freq).astype(int)
+
+    def extra_wavefronts(slots):
+        extra = 0
+        for o in range(32):
+            bins = {int(lut[m]) for m in slots[8 * o:8 * o + 8]}
+            groups = {}
+            for L in bins:
+                groups.setdefault((L ^ ((L >> 3) & 1)) & 7, set()).add(L)
+            extra += max(len(v) for v in groups.values()) - 1
+        return extra
+
+    natural = extra_wavefronts(list(range(256)))
+    ordered = extra_wavefronts(list(order))
+    assert ordered <= 8 and ordered < natural, (ordered, natural)
