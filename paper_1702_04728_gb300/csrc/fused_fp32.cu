@@ -30,6 +30,7 @@
 #include "device_common.cuh"
 
 #include <cstdint>
+#include <mutex>
 
 namespace chimebf {
 namespace {
@@ -518,14 +519,25 @@ __global__ void debug_unpack_kernel(const uint8_t* __restrict__ in, float2* __re
 // Shared-memory opt-in, and a check that the compiled kernel was given the
 // registers per thread the setmaxnreg split assumes: with fewer, the producers'
 // increase could not be granted, so such a build is refused instead of launched.
+// Done once per device (the outcome is kept and returned on every launch).
 template <bool kDump>
 cudaError_t prepare_fp32() {
-    cudaFuncAttributes fa;
-    cudaError_t e = cudaFuncGetAttributes(&fa, fused_fp32_kernel<kDump>);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    if (fa.numRegs < kRegLaunch) return cudaErrorInvalidConfiguration;
-    return cudaFuncSetAttribute(fused_fp32_kernel<kDump>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)kSmemTotal);
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    static std::once_flag once[kMaxDevices];
+    static cudaError_t result[kMaxDevices];
+    std::call_once(once[dev], [&] {
+        cudaFuncAttributes fa;
+        cudaError_t r = cudaFuncGetAttributes(&fa, fused_fp32_kernel<kDump>);
+        if (r == cudaSuccess && fa.numRegs < kRegLaunch) r = cudaErrorInvalidConfiguration;
+        if (r == cudaSuccess)
+            r = cudaFuncSetAttribute(fused_fp32_kernel<kDump>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)kSmemTotal);
+        result[dev] = r;
+    });
+    return result[dev];
 }
 
 cudaError_t fused_fp32_launch(const Batch& b, int grid, cudaStream_t s) {

@@ -33,6 +33,7 @@
 #include <cuda_fp16.h>
 
 #include <cstdint>
+#include <mutex>
 
 namespace chimebf {
 namespace {
@@ -595,8 +596,18 @@ cudaError_t launch_tc(const Batch& b, int grid, cudaStream_t s) {
     if (MODE == 0 && TERMS != 2 && (!b.part || !b.park || !b.part_tok || grid > 2 * kMaxSplit))
         return cudaErrorInvalidValue;
     const int smem = (int)TcCfg<TERMS>::SMEM;
-    cudaError_t e = cudaFuncSetAttribute(fused_tc_kernel<TERMS, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    // shared-memory opt-in, once per device (the outcome is kept and returned on every launch)
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    static std::once_flag once[kMaxDevices];
+    static cudaError_t result[kMaxDevices];
+    std::call_once(once[dev], [&] {
+        result[dev] = cudaFuncSetAttribute(fused_tc_kernel<TERMS, MODE>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    });
+    if (result[dev] != cudaSuccess) return result[dev];
     fused_tc_kernel<TERMS, MODE><<<grid, TcCfg<TERMS>::NT, smem, s>>>(b);
     return cudaGetLastError();
 }
