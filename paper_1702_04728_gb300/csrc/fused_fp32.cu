@@ -514,12 +514,12 @@ __global__ void debug_unpack_kernel(const uint8_t* __restrict__ in, float2* __re
     out[i] = make_float2(re.x, im.x);
 }
 
-}  // namespace
 
 // Shared-memory opt-in, and a check that the compiled kernel was given the
 // registers per thread the setmaxnreg split assumes: with fewer, the producers'
 // increase could not be granted, so such a build is refused instead of launched.
-// Done once per device (the outcome is kept and returned on every launch).
+// Done once per device (the outcome is kept and returned on every launch); the flags
+// have internal linkage, so two copies of the library in one process keep their own.
 template <bool kDump>
 cudaError_t prepare_fp32() {
     int dev = 0;
@@ -539,6 +539,8 @@ cudaError_t prepare_fp32() {
     });
     return result[dev];
 }
+
+}  // namespace
 
 cudaError_t fused_fp32_launch(const Batch& b, int grid, cudaStream_t s) {
     if (b.n_items <= 0) return cudaSuccess;
