@@ -20,6 +20,7 @@
 #include <cstring>
 #include <deque>
 #include <map>
+#include <set>
 #include <memory>
 #include <mutex>
 #include <string>
@@ -250,53 +251,102 @@ uint64_t freq_key(double f) {
 // per lane, eight consecutive lanes at a time; eight beams whose bins fall in
 // distinct 16-byte bank groups (or that share a bin) load without a bank
 // conflict, while the beams' natural order puts several bins of a group into
-// one load.  Any order gives the same result; this one packs, per group of
-// eight slots, beams of distinct bank groups (first fit, largest bin first).
+// one load.  Any order gives the same result.  Beams sharing a bin form units
+// (at most eight beams); units are packed into the 32 groups of eight slots,
+// largest first, by first fit and by best fit under a few orders of the units,
+// and the packing with the fewest conflicts is kept (a conflict: one more
+// distinct bin in a bank group of a slot group).
 void gather_order(const int32_t* lut, int16_t* order) {
-    std::map<int, std::vector<int>> by_bin;
-    for (int m = 0; m < kNs; ++m) by_bin[lut[m]].push_back(m);
+    constexpr int kOct = kNs / 8;
     struct Unit {
-        int group;
+        int bin, group;
         std::vector<int> beams;
     };
+    std::map<int, std::vector<int>> by_bin;
+    for (int m = 0; m < kNs; ++m) by_bin[lut[m]].push_back(m);
     std::vector<Unit> units;
     for (auto& kv : by_bin) {
         const int L = kv.first, sw = L ^ ((L >> 3) & 1);     // the kernel's bin swizzle
         for (size_t i = 0; i < kv.second.size(); i += 8) {
             Unit u;
+            u.bin = L;
             u.group = sw & 7;
             u.beams.assign(kv.second.begin() + i, kv.second.begin() + std::min(kv.second.size(), i + 8));
             units.push_back(std::move(u));
         }
     }
-    std::stable_sort(units.begin(), units.end(),
-                     [](const Unit& a, const Unit& b) { return a.beams.size() > b.beams.size(); });
-    constexpr int kOct = kNs / 8;
-    std::vector<int> members[kOct];
-    unsigned used[kOct] = {};
-    for (const Unit& u : units) {
-        const int n = (int)u.beams.size();
-        int o = 0;
-        while (o < kOct && ((int)members[o].size() + n > 8 || ((used[o] >> u.group) & 1))) ++o;
-        if (o == kOct) {                                   // no conflict-free place: any with room
-            o = 0;
-            while (o < kOct && (int)members[o].size() + n > 8) ++o;
+    auto conflicts = [&](const std::vector<std::vector<int>>& mem) {
+        int extra = 0;
+        for (const auto& o : mem) {
+            std::map<int, std::set<int>> groups;
+            for (int m : o) {
+                const int L = lut[m];
+                groups[(L ^ ((L >> 3) & 1)) & 7].insert(L);
+            }
+            int worst = 1;
+            for (auto& g : groups) worst = std::max(worst, (int)g.second.size());
+            extra += worst - 1;
         }
-        if (o < kOct) {
-            members[o].insert(members[o].end(), u.beams.begin(), u.beams.end());
-            used[o] |= 1u << u.group;
-            continue;
+        return extra;
+    };
+    // one packing of the units in the given order; best = smallest room that fits
+    auto pack = [&](const std::vector<int>& seq, bool best) {
+        std::vector<std::vector<int>> mem(kOct);
+        std::vector<std::map<int, int>> bin_of_group(kOct);     // group -> bin placed there
+        for (int ui : seq) {
+            const Unit& u = units[ui];
+            const int n = (int)u.beams.size();
+            auto fits = [&](int o, bool strict) {
+                if ((int)mem[o].size() + n > 8) return false;
+                if (!strict) return true;
+                auto it = bin_of_group[o].find(u.group);
+                return it == bin_of_group[o].end() || it->second == u.bin;
+            };
+            int pick = -1;
+            for (int strict = 1; strict >= 0 && pick < 0; --strict)
+                for (int o = 0; o < kOct; ++o)
+                    if (fits(o, strict) && (pick < 0 || (best && mem[o].size() > mem[pick].size()))) {
+                        pick = o;
+                        if (!best) break;
+                    }
+            if (pick >= 0) {
+                mem[pick].insert(mem[pick].end(), u.beams.begin(), u.beams.end());
+                bin_of_group[pick].emplace(u.group, u.bin);
+                continue;
+            }
+            for (int m : u.beams) {                        // split over whatever room is left
+                int q = 0;
+                while (mem[q].size() == 8) ++q;
+                mem[q].push_back(m);
+                bin_of_group[q].emplace(u.group, u.bin);
+            }
         }
-        for (int m : u.beams) {                            // split over whatever room is left
-            int q = 0;
-            while (members[q].size() == 8) ++q;
-            members[q].push_back(m);
-            used[q] |= 1u << u.group;
+        return mem;
+    };
+    std::vector<int> seq(units.size());
+    for (size_t i = 0; i < seq.size(); ++i) seq[i] = (int)i;
+    auto by_size = [&](int a, int b) { return units[a].beams.size() > units[b].beams.size(); };
+    std::vector<std::vector<int>> best_mem;
+    int best_c = 1 << 30;
+    uint32_t lcg = 12345u;
+    for (int trial = 0; trial < 8 && best_c > 0; ++trial) {
+        if (trial >= 2) {                                  // deterministic shuffles, then largest first
+            for (size_t i = seq.size(); i > 1; --i) {
+                lcg = lcg * 1664525u + 1013904223u;
+                std::swap(seq[i - 1], seq[(lcg >> 8) % i]);
+            }
+        }
+        std::stable_sort(seq.begin(), seq.end(), by_size);
+        auto mem = pack(seq, (trial & 1) != 0);
+        const int c = conflicts(mem);
+        if (c < best_c) {
+            best_c = c;
+            best_mem = std::move(mem);
         }
     }
     int k = 0;
-    for (int o = 0; o < kOct; ++o)
-        for (int m : members[o]) order[k++] = (int16_t)m;
+    for (const auto& o : best_mem)
+        for (int m : o) order[k++] = (int16_t)m;
 }
 
 int table_for(bf_plan_s* p, double f, int* idx) {
