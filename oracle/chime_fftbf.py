@@ -19,7 +19,7 @@ the fan-beam pipeline of Sec. 3 computes for one coarse frequency channel:
       (3 blocks) cadence (Sec. 3, Table 1).
 
 Readings of points the paper leaves open (each is a plan parameter or a
-convention; they are listed with reasons in the design notes):
+convention chosen where the paper is silent):
 
 * nibble order: high nibble = real, low nibble = imaginary, value = nibble - 8;
 * input order inside a time sample: (cylinder * 256 + feed) * 2 + pol;
@@ -267,36 +267,35 @@ def sky_map(O: np.ndarray) -> np.ndarray:
     return np.asarray(O, dtype=np.float64).sum(axis=(1, 2))
 
 
+def rescale_value(O: np.ndarray):
+    """The unrounded 8-bit code value of every element and the row statistics
+    (Table 1 lists 8-bit integer intensity; the scaling rule is not given).
+    Reading: per (beam, sub-channel) row of frames, the mean and the population
+    standard deviation over the row, v = 64 + 16 (x - mean) / std, i.e. the
+    codes span -4 sigma .. +11.9 sigma in 1/16 sigma steps.  Plain definitions
+    in FP64.  Returns (v float64 like O, constant bool [rows], stats float64
+    [..., 2] = mean, std); v is 64 on a constant row."""
+    X = np.asarray(O, dtype=np.float64).reshape(-1, O.shape[-1])
+    mean = X.mean(axis=1)
+    d = X - mean[:, None]
+    sd = np.sqrt((d * d).mean(axis=1))
+    const = np.all(X == X[:, :1], axis=1)
+    v = np.full(X.shape, 64.0)
+    ok = ~const
+    v[ok] = 64.0 + 16.0 * d[ok] / sd[ok, None]
+    sd = np.where(const, 0.0, sd)
+    stats = np.stack([mean, sd], axis=1)
+    return v.reshape(O.shape), const.reshape(O.shape[:-1]), stats.reshape(O.shape[:-1] + (2,))
+
+
 def rescale_u8(O: np.ndarray):
-    """8-bit output (Table 1 lists 8-bit integer intensity; the scaling rule is
-    not given).  Reading: per (beam, sub-channel) row, the mean and standard
-    deviation over the row's frames, code = clip(floor(64 + 16 z + 1/2), 0, 255)
-    with z = (x - mean) * (1 / std), i.e. -4 sigma .. +11.9 sigma in 1/16 sigma
-    steps; a constant row gets code 64.  Evaluated in FP32 (the precision of the
-    intensity) in a fixed order: sums run frame by frame, each operation
-    rounded once, so the integer codes are reproducible bit for bit.
-    Returns (codes uint8 like O, stats float32 [..., 2] = mean, std)."""
-    X = np.asarray(O, dtype=np.float32).reshape(-1, O.shape[-1])
-    rows, nf = X.shape
-    f32 = np.float32
-    s = np.zeros(rows, f32)
-    for f in range(nf):
-        s = s + X[:, f]
-    mean = s / f32(nf)
-    q = np.zeros(rows, f32)
-    for f in range(nf):
-        d = X[:, f] - mean
-        q = q + d * d
-    sd = np.sqrt(q / f32(nf))
-    pos = sd > 0
-    inv = np.zeros(rows, f32)
-    inv[pos] = f32(1.0) / sd[pos]
-    z = (X - mean[:, None]) * inv[:, None]
-    c = np.floor((f32(64.0) + f32(16.0) * z) + f32(0.5))
-    c[~pos] = 64.0
-    codes = np.clip(c, 0, 255).astype(np.uint8)
-    stats = np.stack([mean, sd], axis=1).astype(f32)
-    return codes.reshape(O.shape), stats.reshape(O.shape[:-1] + (2,))
+    """8-bit output: code = clip(floor(v + 1/2), 0, 255) of rescale_value's v
+    (round half up to the nearest 1/16 sigma step, clipped to one byte); a
+    constant row gets code 64.  Returns (codes uint8 like O, stats float64
+    [..., 2] = mean, std)."""
+    v, _, stats = rescale_value(O)
+    codes = np.clip(np.floor(v + 0.5), 0, 255).astype(np.uint8)
+    return codes, stats
 
 
 K_DM_S_MHZ2 = 4.148808e3        # dispersion constant, s MHz^2 / (pc cm^-3)

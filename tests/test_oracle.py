@@ -364,36 +364,118 @@ def test_brute_force_tiny_geometry(freq):
 # --- products of the output (NEXT items) -------------------------------------------------
 
 def test_rescale_u8_rule():
-    O = np.zeros((2, 3, 8), np.float32)
-    O[0, 0] = 5.0                                        # constant row -> 64
-    O[0, 1] = np.tile([0.0, 1.0], 4)                     # mean 0.5, std 0.5 -> z = -1, +1
-    O[0, 2] = [0, 0, 0, 0, 0, 0, 0, 1000]                # one outlier: z = +sqrt(7) ~ 2.65
-    O[1, 0] = [1000, 1000, 1000, 1000, 1000, 1000, 1000, 0]   # z = -sqrt(7) for the last
-    O[1, 1] = np.arange(8)
-    O[1, 2] = [0, 0, 0, 0, 0, 0, 0, 1e30]                # its squares overflow FP32: codes stay clipped
-    with np.errstate(over="ignore"):
-        codes, stats = O_rescale(O)
-    assert np.all(codes[0, 0] == 64) and stats[0, 0, 1] == 0.0
+    X = np.zeros((2, 4, 8), np.float32)
+    X[0, 0] = 5.0                                        # constant row -> 64
+    X[0, 1] = np.tile([0.0, 1.0], 4)                     # mean 0.5, std 0.5 -> z = -1, +1
+    X[0, 2] = [0, 0, 0, 0, 0, 0, 0, 1000]                # one outlier: z = +sqrt(7) ~ 2.65
+    X[0, 3] = np.float32(0.1)                            # constant row whose FP32 sum is not exact
+    X[1, 0] = [1000, 1000, 1000, 1000, 1000, 1000, 1000, 0]   # z = -sqrt(7) for the last
+    X[1, 1] = np.arange(8)
+    X[1, 2] = [0, 0, 0, 0, 0, 0, 0, 1e30]                # FP64 squares stay finite
+    X[1, 3] = [0, 0, 0, 0, 0, 0, 0, 1e6]                 # z of the zeros -1/sqrt(7), of the peak +sqrt(7)
+    codes, stats = O.rescale_u8(X)
+    assert np.all(codes[0, 0] == 64) and stats[0, 0, 1] == 0.0 and np.all(codes[0, 3] == 64)
     assert np.array_equal(codes[0, 1], np.tile([48, 80], 4))
-    assert codes[0, 2, 7] == int(np.floor(64 + 16 * np.sqrt(7) + 0.5)) and codes[0, 2, 0] == int(np.floor(64 - 16 / np.sqrt(7) + 0.5))
-    assert codes[1, 0, 7] == int(np.floor(64 - 16 * np.sqrt(7) + 0.5))
-    assert np.allclose(stats[1, 1], [3.5, np.std(np.arange(8))])       # population std
-    z = (np.arange(8) - 3.5) / np.std(np.arange(8))
-    assert np.array_equal(codes[1, 1], np.clip(np.floor(64 + 16 * z + 0.5), 0, 255).astype(np.uint8))
-    assert codes[1, 2].max() <= 255 and codes[1, 2].min() >= 0
+    assert codes[0, 2, 7] == int(np.floor(64 + 16 * np.sqrt(7) + 0.5)) == 106
+    assert codes[0, 2, 0] == int(np.floor(64 - 16 / np.sqrt(7) + 0.5)) == 58
+    assert codes[1, 0, 7] == int(np.floor(64 - 16 * np.sqrt(7) + 0.5)) == 22
+    assert np.allclose(stats[1, 1], [3.5, np.sqrt(5.25)], rtol=1e-15)   # population std of 0..7
+    # 0..7: z = (k - 3.5) / sqrt(5.25), v = 64 + 16 z -> 39.6, 46.6, 53.5, 60.5, 67.5, 74.5, 81.4, 88.4
+    assert codes[1, 1].tolist() == [40, 47, 54, 61, 67, 74, 81, 88]
+    assert codes[1, 2].tolist() == [58] * 7 + [106] and np.array_equal(codes[1, 2], codes[1, 3])
+    # range: z = -4 is code 0, z = +11.9 is code 254.4 -> 254; beyond that the codes clip
+    Y = np.zeros((1, 1, 257), np.float64)
+    Y[0, 0, 0] = 1.0                                     # z of the peak = sqrt(256) = 16 -> clipped at 255
+    c, st = O.rescale_u8(Y)
+    assert c[0, 0, 0] == 255 and c[0, 0, 1] == int(np.floor(64 - 16 / 16 + 0.5)) == 63
+    v, const, _ = O.rescale_value(X)
+    assert const.tolist() == [[True, False, False, True], [False, False, False, False]]
+    assert np.all(v[0, 0] == 64.0)
 
 
-def O_rescale(O):
-    return O_mod.rescale_u8(O)
+def test_sky_map_parseval_total_with_dft_tiling():
+    """With pointings on the even bins (L(m) = 2m, the 256-point DFT of the feed
+    line) and DFT-spaced E-W beams (cylinder phase steps of j/4 turn), every
+    transform of the path is unitary up to its length, so the frequency- and
+    time-summed map of ANY input totals 128 x 256 x 4 x sum |x|^2 over the whole
+    frames, |x|^2 taken straight from the nibbles."""
+    f = 610e6
+    d = O.CHIME.feed_spacing_m
+    L = np.where(np.arange(256) < 128, 2 * np.arange(256), 2 * np.arange(256) - 512)
+    ns = L * O.C0 / (512 * f * d)
+    ew = np.arange(4) * O.C0 / (4 * f * O.CHIME.cyl_spacing_m)
+    assert np.array_equal(O.clamp_lut(f, ns), 2 * np.arange(256))
+    raw = rand_raw((2, 384 * 2 + 50, 2048))
+    out = O.beamform(raw, [f, f], ns, ew)
+    smap = O.sky_map(out)
+    b = raw[:, :768].astype(np.int64)
+    power = int((((b >> 4) - 8) ** 2 + ((b & 15) - 8) ** 2).sum())
+    assert smap.shape == (1024,)
+    assert abs(smap.sum() / (128 * 256 * 4 * power) - 1) < 1e-12
 
 
-O_mod = O
+def test_sky_map_of_a_zenith_source_closed_form():
+    """A source at zenith, x = a i^k with quarter-turn phases k per sample and
+    polarisation (exact on the 4-bit grid), summed over channels 400-800 MHz:
+    beam (j, m) holds sum_f 128 x 384 x n_frames x 2 x a^2 |D(L_f(m))|^2 |A_j(f)|^2
+    with D(L) = sum_n exp(-2 pi i n L / 512) (256 at L = 0, 0 at other even L,
+    2 / (1 - exp(-i pi L / 256)) at odd L) and A_j the E-W array factor."""
+    a = 3
+    freqs = [400e6 + 390625.0 * (k + 0.5) for k in (0, 137, 512, 700, 1023)]
+    ns = O.default_ns_sin().copy()
+    ns[128] = 0.0
+    ew = np.array([0.0, np.sin(np.radians(0.2)), np.sin(np.radians(-0.6)), 0.01])
+    T = 384 * 2
+    k = np.random.default_rng(8).integers(0, 4, size=(len(freqs), T, 2))
+    z = a * (1j ** k)                                            # [ch, t, pol]
+    re = np.broadcast_to(np.rint(z.real).astype(int)[:, :, None, None, :], (len(freqs), T, 4, 256, 2))
+    im = np.broadcast_to(np.rint(z.imag).astype(int)[:, :, None, None, :], (len(freqs), T, 4, 256, 2))
+    raw = synth.encode(re, im).reshape(len(freqs), T, 2048)
+    smap = O.sky_map(O.beamform(raw, freqs, ns, ew))
+    expect = np.zeros(1024)
+    n = np.arange(256)
+    for f in freqs:
+        Lf = nearest_beam_bins(f, ns)
+        D = np.array([256.0 if Lm == 0 else (0.0 if Lm % 2 == 0 else abs(2 / (1 - cmath.exp(-1j * math.pi * Lm / 256))))
+                      for Lm in Lf])
+        A = np.abs(np.exp(-2j * np.pi * f * np.outer(np.arange(4) * 20.0, ew) / O.C0).sum(axis=0))   # [j]
+        expect += 128 * T * 2 * a * a * (A[:, None] ** 2 * D[None, :] ** 2).ravel()
+    assert np.allclose(smap, expect, rtol=1e-9, atol=1e-9 * expect.max())
+    assert int(np.argmax(smap)) == 0 * 256 + 128 and abs(smap[128] / (len(freqs) * 128 * T * 2 * (a * 1024) ** 2) - 1) < 1e-12
 
 
-def test_sky_map_sums_subchannels_and_frames():
-    rng_ = np.random.default_rng(3)
-    X = rng_.random((1024, 32, 5))
-    assert np.allclose(O.sky_map(X), X.sum(axis=(1, 2)))
+@pytest.mark.parametrize("f_c", [410e6, 650e6])
+def test_subchannel_freqs_hold_the_tones_that_land_in_them(f_c):
+    """Sec. 3.2 up-channelisation: a coarse-channel sample rotates as
+    exp(+2 pi i delta t dt) for a sky tone at f_c + delta (the sign of the
+    plane-wave convention).  A tone at each of the 128 fine-channel centres
+    must land, whole, in one sub-channel; the sub-channel holding it must be the
+    one whose centre frequency (subchannel_freqs) is nearest the tone, and each
+    sub-channel's centre must be the mean of the eight tones it holds.  A
+    flipped fftshift, a one-sub-channel shift or a half-fine-channel offset of
+    the centres fails one of these."""
+    fine = 390625.0 / 128
+    dt = 2.56e-6
+    centres = O.subchannel_freqs([f_c])
+    assert centres.shape == (16,)
+    held = {s: [] for s in range(16)}
+    tau = np.arange(384)
+    for q in range(128):
+        delta = (q - 64) * fine                               # any integer number of fine channels
+        B = np.exp(2j * np.pi * delta * tau * dt)[:, None, None, None] * np.ones((1, 2, 4, 256))
+        P = O.detect_downsample(O.upchannelize(B))[0, :, 0]   # beam 0, [sub]
+        s = int(np.argmax(P))
+        assert abs(P[s] - P.sum()) <= 1e-9 * P.sum()          # the whole tone in one sub-channel
+        assert s == int(np.argmin(np.abs(centres - (f_c + delta))))
+        held[s].append(f_c + delta)
+    for s in range(16):
+        assert len(held[s]) == 8 and abs(np.mean(held[s]) - centres[s]) < 1e-6
+    # tones between fine-channel centres: negative offsets, and within a quarter of a
+    # fine channel of a sub-channel edge, still go to the nearest centre
+    for delta in (-0.3 * fine, -64.2 * fine, 8 * fine - 0.6 * fine, 23.8 * fine, -8.7 * fine):
+        B = np.exp(2j * np.pi * delta * tau * dt)[:, None, None, None] * np.ones((1, 2, 4, 256))
+        P = O.detect_downsample(O.upchannelize(B))[0, :, 0]
+        assert int(np.argmax(P)) == int(np.argmin(np.abs(centres - (f_c + delta))))
 
 
 def test_dedispersion_aligns_a_synthetic_sweep():
