@@ -94,6 +94,11 @@ typedef struct {
     void* cuda_stream;      /* cudaStream_t for the launches, or NULL: the plan
                                creates its own non-blocking stream                */
     int device;             /* CUDA device ordinal, or -1 for the current device  */
+    int max_tables;         /* per-frequency table slots (clamp table, E-W phases,
+                               tensor-core twiddle image) held at once, 0 = 4096
+                               (the largest); a new frequency reuses the least
+                               recently used slot that no open stream and no
+                               running batch references, else BF_ENOMEM          */
 } bf_config;
 
 /* Fill *cfg with the CHIME defaults above.  Returns BF_OK or BF_EINVAL. */
@@ -187,20 +192,26 @@ int bf_dedisperse(bf_plan_t p, const float* d_out, int n_chan, const double* cha
                   double dm, float* d_series, int64_t* n_out);
 
 /*
- * bf_dedisperse without any device allocation (the paper has no counterpart:
- * this serves callers that may not allocate, e.g. around CUDA graph capture).
- * Same arguments, rule and result as bf_dedisperse, for n_chan <= 4096 (at
- * most 65536 sub-channels; more is rejected with BF_EINVAL before any work).
- * The delay table lives in one file-scope device array of 65536 ints
- * (256 KB) per device:
+ * bf_dedisperse without any device allocation (the paper has no counterpart).
+ * bf_dedisperse keeps its delay table in plan memory that it grows with
+ * cudaFree + cudaMalloc, and cudaFree waits for the whole device; callers whose
+ * device memory is owned by someone else (a framework's pool reserved up
+ * front, an embedding application that forbids allocation after start-up) or
+ * that run a latency-bound loop beside other streams cannot make those calls.
+ * This entry point takes the same arguments and gives the same result, for
+ * n_chan <= 4096 (at most 65536 sub-channels; more is rejected with BF_EINVAL
+ * before any work).  The delay table lives in one file-scope device array of
+ * 65536 ints (256 KB) that every device loading the library holds until the
+ * process exits:
  *   - the array is shared by every plan and thread of the process on that
- *     device, so overlapping calls (other streams or threads) race on it;
+ *     device, so calls that overlap on the GPU (other streams or threads) race
+ *     on it; serialise them;
  *   - it keeps the last call's delays; nothing in it has to start at zero,
- *     because each call writes the n_chan * 16 entries it reads before its
- *     kernel runs (in stream order on the plan's stream);
+ *     because each call writes the n_chan * 16 entries it reads (a copy from
+ *     host memory, in stream order on the plan's stream) before its kernel runs;
  *   - the first call on a device looks the array's address up
- *     (cudaGetSymbolAddress, device current, return code checked): make that
- *     first call before any stream capture that includes this entry point.
+ *     (cudaGetSymbolAddress, with the device current, return code checked);
+ *     make that first call before any stream capture.
  * No cudaMalloc, cudaFree or other allocating call is made.
  */
 int bf_dedisperse_static(bf_plan_t p, const float* d_out, int n_chan, const double* chan_freq_hz,
@@ -263,6 +274,20 @@ int bf_debug_beams(bf_plan_t p, double freq_hz, const uint8_t* d_vin, int64_t n_
  * [block][pol][ew][ns][q'] (q' fftshifted) for n_samples a multiple of 384,
  * computed by the fused kernel with detection replaced by a dump. */
 int bf_debug_upchan(bf_plan_t p, double freq_hz, const uint8_t* d_vin, int64_t n_samples, float* d_out);
+
+/* ---- measurement aid (no counterpart in the paper) ------------------------ */
+
+/* Throughput probe of the FP32 FMA pipe, the unit that bounds the FP32 form:
+ * enqueues on cuda_stream (cudaStream_t; NULL = the legacy default stream) one
+ * kernel of 4 CTAs per SM (at most n_sink / 256 CTAs) x 256 threads on the
+ * current device; each thread runs iters (rounded up to a multiple of 4) steps
+ * of 8 independent packed FFMA2 chains (paired != 0) or 16 scalar FFMA chains,
+ * so the pipe and not latency sets the rate.  d_sink: device float [n_sink],
+ * n_sink >= 256, caller-owned, receives one value per thread.  *flop_out = the
+ * flops the kernel issues (2 per FMA); the caller times the launch on its
+ * stream.  Returns at once. */
+int bf_fp32_fma_probe(void* cuda_stream, int paired, int64_t iters, float* d_sink, int64_t n_sink,
+                      double* flop_out);
 
 #ifdef __cplusplus
 }

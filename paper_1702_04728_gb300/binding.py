@@ -24,7 +24,7 @@ N_BEAMS, N_SUB, FRAME, N_INPUT = 1024, 16, 384, 2048
 
 SYMBOLS = ["bf_config_default", "bf_plan", "bf_frames_out", "bf_submit", "bf_poll", "bf_destroy",
            "bf_last_error", "bf_skymap", "bf_rescale_u8", "bf_dedisperse", "bf_debug_tables", "bf_debug_gather_order", "bf_debug_gemm", "bf_debug_unpack", "bf_debug_beams",
-           "bf_debug_upchan", "bf_debug_stall", "bf_dedisperse_static"]
+           "bf_debug_upchan", "bf_debug_stall", "bf_dedisperse_static", "bf_fp32_fma_probe"]
 
 
 class BfError(RuntimeError):
@@ -41,7 +41,8 @@ class bf_config(ctypes.Structure):
                 ("dt_s", ctypes.c_double),
                 ("ns_sin", ctypes.POINTER(ctypes.c_double)), ("ew_sin", ctypes.POINTER(ctypes.c_double)),
                 ("form", ctypes.c_int), ("mode", ctypes.c_int), ("mem_budget", ctypes.c_size_t),
-                ("max_streams", ctypes.c_int), ("cuda_stream", ctypes.c_void_p), ("device", ctypes.c_int)]
+                ("max_streams", ctypes.c_int), ("cuda_stream", ctypes.c_void_p), ("device", ctypes.c_int),
+                ("max_tables", ctypes.c_int)]
 
 
 class bf_request(ctypes.Structure):
@@ -83,6 +84,7 @@ def lib() -> ctypes.CDLL:
         L.bf_rescale_u8.argtypes = [P, P, I64, I64, P, P]
         L.bf_dedisperse.argtypes = [P, P, I, ctypes.POINTER(D), I64, D, P, ctypes.POINTER(I64)]
         L.bf_dedisperse_static.argtypes = [P, P, I, ctypes.POINTER(D), I64, D, P, ctypes.POINTER(I64)]
+        L.bf_fp32_fma_probe.argtypes = [P, I, I64, P, I64, ctypes.POINTER(D)]
         for name in SYMBOLS:
             getattr(L, name).restype = ctypes.c_char_p if name == "bf_last_error" else I
         _lib = L
@@ -249,6 +251,14 @@ def bf_dedisperse_static(plan: int, d_out, freqs, n_frames: int, dm: float, d_se
 
 def bf_rescale_u8(plan: int, d_out, n_rows: int, n_frames: int, d_codes, d_stats=None) -> None:
     _check(lib().bf_rescale_u8(plan, _ptr(d_out), n_rows, n_frames, _ptr(d_codes), _ptr(d_stats)))
+
+
+def bf_fp32_fma_probe(stream, paired: bool, iters: int, d_sink, n_sink: int) -> float:
+    """Enqueue the FP32 FMA-pipe probe on `stream`; returns the flops it issues."""
+    f = ctypes.c_double()
+    _check(lib().bf_fp32_fma_probe(stream_handle(stream), 1 if paired else 0, int(iters), _ptr(d_sink),
+                                   int(n_sink), ctypes.byref(f)))
+    return f.value
 
 
 # ---- convenience over torch device memory (allocation and marshalling only) ----

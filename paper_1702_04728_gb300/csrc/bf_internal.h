@@ -41,6 +41,7 @@ struct Seg {
     int item_begin;          // first work item; 4 items (E-W beams) per frame
     int pad_;
     const float2* ew_frames; // tracking E-W beams: [n_frames][4 ew][4 cyl] phases, or null (static)
+    const unsigned char* a_img;  // tensor-core form: FP16 twiddle image(s) of this segment's table
 };
 
 struct Batch {
@@ -52,8 +53,6 @@ struct Batch {
     const float2* tw512;     // [512] exp(-2 pi i e / 512)
     const float2* tw128;     // [128] exp(-2 pi i e / 128)
     float2* dump;            // debug: up-channelised voltages instead of detection
-    const unsigned char* a_tc;   // tensor-core form: FP16 twiddle images per table
-    size_t a_tc_stride;          // bytes per table in a_tc
     int* status;                 // set non-zero by a kernel whose bounded wait expired
     unsigned long long wait_ns;  // bound on each device-side wait (0: the default, 2 s)
     float* part;                 // halves of split items [grid / 2 + 1][2][16][256] (null: no split)
@@ -88,5 +87,9 @@ cudaError_t dedisperse_static_table(int device, int** table);
 cudaError_t rescale_u8_launch(const float* in, long long rows, long long nf, uint8_t* codes, float* stats,
                               cudaStream_t s);
 int tc_chunk_k(int terms);       // K elements per shared-memory chunk
+// FP32 FMA-pipe probe: 4 CTAs per SM (at most n_sink / 256) of 256 threads, each
+// thread `iters` (rounded up to 4) x 8 FFMA2 (paired) or 16 scalar FMA; *flop = flops issued.
+cudaError_t fma_probe_launch(bool paired, long long iters, float* sink, long long n_sink, int sms, double* flop,
+                             cudaStream_t s);
 
 }  // namespace chimebf

@@ -391,21 +391,21 @@ __global__ void __launch_bounds__(TcCfg<TERMS>::NT, 1) fused_tc_kernel(const __g
             long long c_copy = 0;                             // next twiddle chunk to copy
             const long long whole_chunks = (long long)n_my_whole * PASSES * C::NCH;
             const long long total = whole_chunks + (long long)(n_my_units - n_my_whole) * (PASSES / 2) * C::NCH;
-            // table of the item that chunk cc belongs to; items only move forward, so
-            // the segment search resumes where the previous lookup stopped
+            // twiddle image of the item that chunk cc belongs to; items only move forward,
+            // so the segment search resumes where the previous lookup stopped
             int seg_cursor = 0;
-            auto table_of = [&](long long cc) {
+            auto image_of = [&](long long cc) {
                 const int k = cc < whole_chunks
                                   ? (int)(cc / (PASSES * C::NCH))
                                   : n_my_whole + (int)((cc - whole_chunks) / ((PASSES / 2) * C::NCH));
                 int it, ps0, ps1, half;
                 unit_of(units, (int)blockIdx.x + k * (int)gridDim.x, it, ps0, ps1, half);
                 while (seg_cursor + 1 < bt.n_segs && bt.segs[seg_cursor + 1].item_begin <= it) ++seg_cursor;
-                return bt.segs[seg_cursor].table;
+                return bt.segs[seg_cursor].a_img;
             };
             auto issue_copy = [&](long long cc) {
                 const int a = (int)(cc % NA), kc = (int)(cc % C::NCH);
-                const unsigned char* a_hi = bt.a_tc + (size_t)table_of(cc) * bt.a_tc_stride;
+                const unsigned char* a_hi = image_of(cc);
                 unsigned char* st = a_ring + a * C::A_STAGE;
                 mbar_expect(afull(a), C::A_STAGE);
                 bulk_g2s(smem0 + (uint32_t)(st - smem), a_hi + (size_t)kc * C::OPER, C::OPER, afull(a));

@@ -3,6 +3,7 @@
 // rescaling of the intensity listed in Table 1.
 #include "bf_internal.h"
 
+#include <algorithm>
 #include <cstdint>
 #include <mutex>
 
@@ -42,11 +43,13 @@ __global__ void __launch_bounds__(kMapThreads) skymap_kernel(const float* __rest
     }
 }
 
-// One thread per (beam, sub-channel) row: mean and standard deviation over the
-// row's frames, then code = clip(floor(64 + 16 (x - mean) (1 / std) + 1/2), 0,
-// 255).  FP32, sums frame by frame, every operation rounded once (the _rn
-// intrinsics keep the compiler from fusing multiply and add), so the codes
-// follow a fixed evaluation order.  A CTA stages its 32 rows through shared
+// One thread per (beam, sub-channel) row: mean and population standard
+// deviation over the row's frames, then code = clip(floor(64 + 16 (x - mean) /
+// std + 1/2), 0, 255), a constant row giving 64.  FP32: the sums run over x -
+// x0 (x0 = the row's first frame), which keeps a constant row exactly constant
+// (mean = x0, std = 0) and makes the rounding error of the mean scale with the
+// row's spread instead of its level.  Valid for |x - mean| below ~1e18 (the
+// squares stay finite).  A CTA stages its 32 rows through shared
 // memory with coalesced loads; when the row length is a multiple of 4 (and the
 // code array 4-byte aligned) the codes
 // go back through shared memory as 32-bit words (rows padded by one word, no
@@ -89,26 +92,24 @@ __global__ void __launch_bounds__(kU8Rows) rescale_u8_kernel(const float* __rest
     if (r < rows) {
         const float* x = in + r * nf;
         auto val = [&](long long f) -> float { return staged ? st[threadIdx.x][f] : __ldg(x + f); };
+        const float x0 = val(0);
         float s = 0.f;
-        for (long long f = 0; f < nf; ++f) s = __fadd_rn(s, val(f));
-        const float mean = __fdiv_rn(s, (float)nf);
+        for (long long f = 1; f < nf; ++f) s += val(f) - x0;
+        const float mean = x0 + s / (float)nf;
         float q = 0.f;
         for (long long f = 0; f < nf; ++f) {
-            const float d = __fsub_rn(val(f), mean);
-            q = __fadd_rn(q, __fmul_rn(d, d));
+            const float d = val(f) - mean;
+            q = fmaf(d, d, q);
         }
-        const float sd = __fsqrt_rn(__fdiv_rn(q, (float)nf));
+        const float sd = sqrtf(q / (float)nf);
         if (stats) {
             stats[2 * r] = mean;
             stats[2 * r + 1] = sd;
         }
-        const float inv = sd > 0.f ? __fdiv_rn(1.f, sd) : 0.f;
+        const float scale = sd > 0.f ? 16.f / sd : 0.f;
         auto code = [&](long long f) -> uint32_t {
             float v = 64.f;
-            if (sd > 0.f) {
-                const float z = __fmul_rn(__fsub_rn(val(f), mean), inv);
-                v = floorf(__fadd_rn(__fadd_rn(64.f, __fmul_rn(16.f, z)), 0.5f));
-            }
+            if (sd > 0.f) v = floorf(fmaf(val(f) - mean, scale, 64.5f));
             v = v < 0.f ? 0.f : (v > 255.f ? 255.f : v);
             return (uint32_t)v;
         };
@@ -150,6 +151,42 @@ __global__ void dedisperse_kernel(const float* __restrict__ in, const int* __res
 // device, shared by every plan of the process (see bf_dedisperse_static).
 __device__ __align__(256) int g_dd_delays[kDdStaticMaxSub];
 
+
+// FP32 FMA-pipe probe: every thread runs kProbeChains independent chains of
+// packed (FFMA2) or scalar FMAs, so the pipe, not latency, sets the rate.  The
+// chains converge to c / (1 - b) and stay finite; their sum is stored so that
+// no FMA can be removed.
+constexpr int kProbeThreads = 256;
+constexpr int kProbeChains = 8;
+
+template <bool kPair>
+__global__ void __launch_bounds__(kProbeThreads) fma_probe_kernel(long long iters, float* __restrict__ sink) {
+    float2 a[kProbeChains];
+    const float t = 1e-3f * (float)(threadIdx.x & 31);
+#pragma unroll
+    for (int k = 0; k < kProbeChains; ++k) a[k] = make_float2(t + (float)k, t - (float)k);
+    const float2 b = make_float2(0.9999f, 0.99991f), c = make_float2(1e-4f, 2e-4f);
+#pragma unroll 1
+    for (long long i = 0; i < iters; i += 4) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+#pragma unroll
+            for (int k = 0; k < kProbeChains; ++k) {
+                if constexpr (kPair) {
+                    a[k] = __ffma2_rn(a[k], b, c);
+                } else {
+                    a[k].x = __fmaf_rn(a[k].x, b.x, c.x);
+                    a[k].y = __fmaf_rn(a[k].y, b.y, c.y);
+                }
+            }
+        }
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int k = 0; k < kProbeChains; ++k) s += a[k].x + a[k].y;
+    sink[(long long)blockIdx.x * kProbeThreads + threadIdx.x] = s;
+}
+
 }  // namespace
 
 cudaError_t dedisperse_static_table(int device, int** table) {
@@ -179,6 +216,19 @@ cudaError_t dedisperse_launch(const float* in, const int* delays, int n_sub, lon
 cudaError_t skymap_launch(const float* in, int n_beams, long long per_beam, float* map, cudaStream_t s) {
     if (n_beams <= 0) return cudaSuccess;
     skymap_kernel<<<n_beams, kMapThreads, 0, s>>>(in, per_beam, map);
+    return cudaGetLastError();
+}
+
+cudaError_t fma_probe_launch(bool paired, long long iters, float* sink, long long n_sink, int sms, double* flop,
+                             cudaStream_t s) {
+    const long long blocks = std::min<long long>(4LL * sms, n_sink / kProbeThreads);
+    if (blocks <= 0 || iters <= 0) return cudaErrorInvalidValue;
+    const long long it4 = (iters + 3) / 4 * 4;
+    *flop = (double)blocks * kProbeThreads * (double)it4 * kProbeChains * 4.0;
+    if (paired)
+        fma_probe_kernel<true><<<(unsigned)blocks, kProbeThreads, 0, s>>>(it4, sink);
+    else
+        fma_probe_kernel<false><<<(unsigned)blocks, kProbeThreads, 0, s>>>(it4, sink);
     return cudaGetLastError();
 }
 

@@ -34,8 +34,8 @@ namespace {
 
 constexpr double kC0 = 299792458.0;
 constexpr double kPi = 3.14159265358979323846;
-constexpr int kTableCap = 4096;
-constexpr int kTcTableCap = 512;       // tensor-core twiddle images held at once
+constexpr int kTableCap = 4096;        // default and largest number of per-frequency table slots
+constexpr int kTcBlock = 64;           // tensor-core twiddle images are allocated 64 slots at a time
 constexpr int kMaxInflight = 4;
 
 thread_local std::string g_err;
@@ -96,6 +96,7 @@ struct InflightBatch {
     size_t bytes;
     std::vector<std::pair<size_t, uint8_t*>> release;   // carry buffers free once the batch is done
     TrackBuf track;                                     // tracking tables, back to the pool at retire
+    std::vector<int> slots;                             // table slots the batch reads (one reference each)
 };
 
 }  // namespace
@@ -113,9 +114,19 @@ struct bf_plan_s {
     float2* d_ew = nullptr;
     float2* d_tw512 = nullptr;
     float2* d_tw128 = nullptr;
+    // Per-frequency table slots (clamp table, gather order, E-W phases and, for the
+    // tensor-core form, the FP16 twiddle image).  A slot is referenced by every open
+    // stream that uses its frequency and by every unretired batch that reads it; a
+    // new frequency takes a free slot, else the least recently used unreferenced one.
     std::map<uint64_t, int> table_of_freq;   // key: bit pattern of the double
+    int table_cap = kTableCap;
+    int n_slots = 0;                          // slots filled so far (< table_cap: a fresh one is free)
+    std::vector<uint64_t> slot_key;
+    std::vector<int> slot_refs;
+    std::vector<uint64_t> slot_used;          // LRU clock of the slot's last lookup
+    uint64_t lru_clock = 0;
     int terms = 0;                            // tensor-core GEMM terms (0: FP32 FFT form)
-    unsigned char* d_atc = nullptr;           // [kTcTableCap][tc_a_bytes(terms)] FP16 twiddle images
+    std::vector<unsigned char*> atc_blocks;   // [kTcBlock][tc_a_bytes(terms)] FP16 twiddle images each
     int* h_status = nullptr;                  // mapped status word written by kernels
     int* d_delays = nullptr;                  // dedispersion delay table (grown on demand)
     size_t delays_cap = 0;
@@ -349,37 +360,89 @@ void gather_order(const int32_t* lut, int16_t* order) {
         for (int m : o) order[k++] = (int16_t)m;
 }
 
+const unsigned char* tc_image(const bf_plan_s* p, int slot) {
+    if (!p->terms) return nullptr;
+    return p->atc_blocks[slot / kTcBlock] + (size_t)(slot % kTcBlock) * tc_a_bytes(p->terms);
+}
+
+// Slot holding the tables of frequency f, filled on first use (caller holds the lock).
+// A new frequency takes a never-used slot while there is one, else the least
+// recently used slot that no open stream and no unretired batch references.
 int table_for(bf_plan_s* p, double f, int* idx) {
-    auto it = p->table_of_freq.find(freq_key(f));
+    const uint64_t key = freq_key(f);
+    auto it = p->table_of_freq.find(key);
     if (it != p->table_of_freq.end()) {
         *idx = it->second;
+        p->slot_used[*idx] = ++p->lru_clock;
         return BF_OK;
     }
-    const int n = (int)p->table_of_freq.size();
-    if (n >= kTableCap) return fail(BF_ENOMEM, "too many distinct channel frequencies in one plan");
+    int n = -1;
+    if (p->n_slots < p->table_cap) {
+        n = p->n_slots;
+    } else {
+        for (int i = 0; i < p->table_cap; ++i)
+            if (p->slot_refs[i] == 0 && (n < 0 || p->slot_used[i] < p->slot_used[n])) n = i;
+        if (n < 0)
+            return fail(BF_ENOMEM, "every per-frequency table slot is held by an open stream or a running batch "
+                                   "(raise bf_config.max_tables)");
+    }
     int32_t lut[kNs];
     int16_t lut16[kNs];
     float ew[2 * kEw * kCyl];
     clamp_table(p, f, lut);
     for (int m = 0; m < kNs; ++m) lut16[m] = (int16_t)lut[m];
     ew_table(p, f, ew);
-    CK(cudaMemcpy(p->d_lut + (size_t)n * kNs, lut16, sizeof lut16, cudaMemcpyHostToDevice));
     int16_t order[kNs];
     gather_order(lut, order);
+    if (p->terms) {
+        const int blk = n / kTcBlock;
+        if (!p->atc_blocks[blk]) CK(cudaMalloc(&p->atc_blocks[blk], (size_t)kTcBlock * tc_a_bytes(p->terms)));
+    }
+    // the slot is unreferenced: no launched kernel reads it, so plain copies can refill it
+    if (n < p->n_slots) p->table_of_freq.erase(p->slot_key[n]);
+    CK(cudaMemcpy(p->d_lut + (size_t)n * kNs, lut16, sizeof lut16, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(p->d_order + (size_t)n * kNs, order, sizeof order, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(p->d_ew + (size_t)n * kEw * kCyl, ew, sizeof ew, cudaMemcpyHostToDevice));
     if (p->terms) {
-        if (n >= kTcTableCap) return fail(BF_ENOMEM, "too many distinct channel frequencies for the tensor-core form");
-        if (!p->d_atc) CK(cudaMalloc(&p->d_atc, (size_t)kTcTableCap * tc_a_bytes(p->terms)));
         std::vector<__half> img;
         tc_image(p->terms, lut, img);
-        CK(cudaMemcpy(p->d_atc + (size_t)n * tc_a_bytes(p->terms), img.data(), img.size() * sizeof(__half),
+        CK(cudaMemcpy(const_cast<unsigned char*>(tc_image(p, n)), img.data(), img.size() * sizeof(__half),
                       cudaMemcpyHostToDevice));
     }
-    p->table_of_freq[freq_key(f)] = n;
+    if (n == p->n_slots) ++p->n_slots;
+    p->slot_key[n] = key;
+    p->slot_used[n] = ++p->lru_clock;
+    p->table_of_freq[key] = n;
     *idx = n;
     return BF_OK;
 }
+
+// table_for plus one reference, for work that reads the slot outside the lock.
+int hold_table(bf_plan_s* p, double f, int* idx) {
+    int rc = table_for(p, f, idx);
+    if (rc == BF_OK) ++p->slot_refs[*idx];
+    return rc;
+}
+
+void release_table(bf_plan_s* p, int idx) {
+    if (idx >= 0 && idx < (int)p->slot_refs.size() && p->slot_refs[idx] > 0) --p->slot_refs[idx];
+}
+
+// One reference on a table slot for the length of a synchronous inspection call.
+struct TableHold {
+    bf_plan_s* p;
+    int idx = -1;
+    explicit TableHold(bf_plan_s* plan) : p(plan) {}
+    int take(double f) {
+        std::lock_guard<std::mutex> lk(p->mu);
+        return hold_table(p, f, &idx);
+    }
+    ~TableHold() {
+        if (idx < 0) return;
+        std::lock_guard<std::mutex> lk(p->mu);
+        release_table(p, idx);
+    }
+};
 
 Batch make_batch(const bf_plan_s* p) {
     Batch b;
@@ -389,8 +452,6 @@ Batch make_batch(const bf_plan_s* p) {
     b.ew = p->d_ew;
     b.tw512 = p->d_tw512;
     b.tw128 = p->d_tw128;
-    b.a_tc = p->d_atc;
-    b.a_tc_stride = p->terms ? tc_a_bytes(p->terms) : 0;
     b.status = p->d_status;
     b.part = p->d_part;
     b.part_tok = p->d_part_tok;
@@ -451,8 +512,12 @@ int stream_for(bf_plan_s* p, const bf_request* r, StreamState** out) {
     s.n_chan = r->n_chan;
     s.tables.resize(r->n_chan);
     for (int c = 0; c < r->n_chan; ++c) {
-        int rc = table_for(p, r->chan_freq_hz[c], &s.tables[c]);
-        if (rc) return rc;
+        // each channel's slot is referenced at once, so a later channel cannot evict it
+        int rc = hold_table(p, r->chan_freq_hz[c], &s.tables[c]);
+        if (rc) {
+            for (int k = 0; k < c; ++k) release_table(p, s.tables[k]);
+            return rc;
+        }
     }
     s.carry_bytes = (size_t)r->n_chan * (kFrame - 1) * kInput;   // allocated when first needed
     auto res = p->streams.emplace(r->stream_id, std::move(s));
@@ -487,16 +552,22 @@ int launch_jobs(bf_plan_s* p, std::vector<Job>& jobs, size_t bytes) {
         if (rc) return rc;
     }
     size_t track_off = 0;
+    // table slots the launches read, one reference each; an error before the first launch
+    // drops them again (after it, a launched kernel may read them, so they stay held)
+    std::vector<int> held;
+    auto unhold = [&](int rc) {
+        for (int t : held) release_table(p, t);
+        if (tb.host) p->track_pool.emplace(tb.bytes, tb);
+        return rc;
+    };
     for (auto& jb : jobs) {
         StreamState* st = nullptr;
         int rc = stream_for(p, &jb.req, &st);
-        if (rc) return rc;
+        if (rc) return unhold(rc);
         const int64_t nf = frames_for(p, &jb.req, st->carry_rows);
         const int new_rows = (int)((st->carry_rows + jb.req.n_samples) % kFrame);
-        if (jb.track_frames >= 0 && jb.track_frames != nf) {
-            if (tb.host) p->track_pool.emplace(tb.bytes, tb);
-            return fail(BF_EINVAL, "tracking table rows differ from the frames the request produces");
-        }
+        if (jb.track_frames >= 0 && jb.track_frames != nf)
+            return unhold(fail(BF_EINVAL, "tracking table rows differ from the frames the request produces"));
         const float2* track_dev = nullptr;
         if (!jb.track.empty()) {
             std::memcpy(tb.host + track_off, jb.track.data(), jb.track.size() * sizeof(float2));
@@ -518,6 +589,9 @@ int launch_jobs(bf_plan_s* p, std::vector<Job>& jobs, size_t bytes) {
             s.carry_rows = st->carry_rows;
             s.n_frames = (int)nf;
             s.table = st->tables[c];
+            s.a_img = tc_image(p, s.table);
+            held.push_back(s.table);
+            ++p->slot_refs[s.table];
             s.ew_frames = track_dev ? track_dev + (size_t)c * nf * kEw * kCyl : nullptr;
             s.item_begin = b.n_items;
             b.n_items += (int)nf * kEw;
@@ -530,13 +604,9 @@ int launch_jobs(bf_plan_s* p, std::vector<Job>& jobs, size_t bytes) {
     if (track_elems) {
         cudaError_t e = cudaMemcpyAsync(tb.dev, tb.host, track_elems * sizeof(float2), cudaMemcpyHostToDevice,
                                         p->stream);
-        if (e != cudaSuccess) {
-            p->track_pool.emplace(tb.bytes, tb);
-            return cuda_fail(e, "tracking table upload");
-        }
+        if (e != cudaSuccess) return unhold(cuda_fail(e, "tracking table upload"));
     }
     for (auto& bb : batches) {
-        bb.a_tc = p->d_atc;                       // tables may have been created above
         bb.epoch = ++p->launches;
         // a launch of at most half a grid of items runs every item as two halves on two CTAs
         // (the 2-term tensor-core form never splits)
@@ -576,7 +646,7 @@ int launch_jobs(bf_plan_s* p, std::vector<Job>& jobs, size_t bytes) {
         CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
     }
     CK(cudaEventRecord(ev, p->stream));
-    InflightBatch ib{p->next_batch++, ev, {}, bytes, {}, tb};
+    InflightBatch ib{p->next_batch++, ev, {}, bytes, {}, tb, std::move(held)};
     for (auto& jb : jobs) {
         ib.tickets.push_back(jb.ticket);
         Ticket& t = p->tickets[jb.ticket];
@@ -586,6 +656,7 @@ int launch_jobs(bf_plan_s* p, std::vector<Job>& jobs, size_t bytes) {
     for (auto& c : carries) {
         if (c.drop) {
             if (c.st->carry) ib.release.emplace_back(c.st->carry_bytes, c.st->carry);
+            for (int t : c.st->tables) release_table(p, t);
             p->streams.erase(c.sid);
         }
     }
@@ -620,6 +691,7 @@ bool retire(bf_plan_s* p) {
         p->mem_in_use -= std::min(p->mem_in_use, ib.bytes);
         for (auto& r : ib.release) p->carry_pool.emplace(r.first, r.second);
         if (ib.track.host) p->track_pool.emplace(ib.track.bytes, ib.track);
+        for (int t : ib.slots) release_table(p, t);
         p->event_pool.push_back(ib.ev);
         p->inflight.pop_front();
         any = true;
@@ -726,6 +798,8 @@ int bf_plan(const bf_config* cfg, bf_plan_t* out) {
         return fail(BF_EINVAL, "unknown form");
     if (cfg->mode != BF_MODE_DIRECT && cfg->mode != BF_MODE_SERVING) return fail(BF_EINVAL, "bad mode");
     if (cfg->max_streams < 0) return fail(BF_EINVAL, "negative max_streams");
+    if (cfg->max_tables < 0 || cfg->max_tables > kTableCap)
+        return fail(BF_EINVAL, "max_tables must be 0 (default 4096) or 1 .. 4096");
 
     std::unique_ptr<bf_plan_s> p(new bf_plan_s);
     p->cfg = *cfg;
@@ -758,9 +832,14 @@ int bf_plan(const bf_config* cfg, bf_plan_t* out) {
         CK(cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking));
         p->own_stream = true;
     }
-    CK(cudaMalloc(&p->d_lut, (size_t)kTableCap * kNs * sizeof(int16_t)));
-    CK(cudaMalloc(&p->d_order, (size_t)kTableCap * kNs * sizeof(int16_t)));
-    CK(cudaMalloc(&p->d_ew, (size_t)kTableCap * kEw * kCyl * sizeof(float2)));
+    p->table_cap = cfg->max_tables > 0 ? cfg->max_tables : kTableCap;
+    p->slot_key.assign(p->table_cap, 0);
+    p->slot_refs.assign(p->table_cap, 0);
+    p->slot_used.assign(p->table_cap, 0);
+    p->atc_blocks.assign((p->table_cap + kTcBlock - 1) / kTcBlock, nullptr);
+    CK(cudaMalloc(&p->d_lut, (size_t)p->table_cap * kNs * sizeof(int16_t)));
+    CK(cudaMalloc(&p->d_order, (size_t)p->table_cap * kNs * sizeof(int16_t)));
+    CK(cudaMalloc(&p->d_ew, (size_t)p->table_cap * kEw * kCyl * sizeof(float2)));
     CK(cudaMalloc(&p->d_tw512, kBins * sizeof(float2)));
     CK(cudaMalloc(&p->d_tw128, kUp * sizeof(float2)));
     std::vector<float2> tw(kBins);
@@ -931,7 +1010,8 @@ int bf_destroy(bf_plan_t p) {
     cudaFree(p->d_part);
     cudaFree(p->d_part_tok);
     cudaFree(p->d_park);
-    if (p->d_atc) cudaFree(p->d_atc);
+    for (unsigned char* blk : p->atc_blocks)
+        if (blk) cudaFree(blk);
     if (p->d_delays) cudaFree(p->d_delays);
     if (p->h_status) cudaFreeHost(p->h_status);
     if (p->own_stream) cudaStreamDestroy(p->stream);
@@ -1011,7 +1091,7 @@ int bf_dedisperse_static(bf_plan_t p, const float* d_out, int n_chan, const doub
                          int64_t n_frames, double dm, float* d_series, int64_t* n_out) {
     if (!p || n_chan <= 0 || !chan_freq_hz || n_frames < 0 || !n_out || !(dm >= 0) || !std::isfinite(dm))
         return fail(BF_EINVAL, "bad argument");
-    if (kSub * n_chan > kDdStaticMaxSub)
+    if (n_chan > kDdStaticMaxSub / kSub)         // checked before any product, so no overflow
         return fail(BF_EINVAL, "more channels than the static delay table holds (4096 channels, 65536 sub-channels)");
     const int n_sub = kSub * n_chan;
     std::vector<int> d(n_sub);
@@ -1081,12 +1161,10 @@ int bf_debug_beams(bf_plan_t p, double freq_hz, const uint8_t* d_vin, int64_t n_
         return fail(BF_EINVAL, "bad argument");
     if (((uintptr_t)d_vin & 15) != 0) return fail(BF_EINVAL, "vin must be 16-byte aligned");
     CK(cudaSetDevice(p->device));
-    int tab;
-    {
-        std::lock_guard<std::mutex> lk(p->mu);
-        int rc = table_for(p, freq_hz, &tab);
-        if (rc) return rc;
-    }
+    TableHold hold(p);
+    int rc = hold.take(freq_hz);
+    if (rc) return rc;
+    const int tab = hold.idx;
     CK(debug_beams_launch(d_vin, n_samples, p->d_lut + (size_t)tab * kNs, p->d_ew + (size_t)tab * kEw * kCyl,
                           p->d_tw512, reinterpret_cast<float2*>(d_out), p->stream));
     CK(cudaStreamSynchronize(p->stream));
@@ -1101,12 +1179,11 @@ static int debug_fused(bf_plan_t p, double freq_hz, const uint8_t* d_vin, int64_
     if (mode == 2 && !p->terms) return fail(BF_EINVAL, "the GEMM dump needs a tensor-core form");
     CK(cudaSetDevice(p->device));
     Batch b = make_batch(p);
-    {
-        std::lock_guard<std::mutex> lk(p->mu);
-        int rc = table_for(p, freq_hz, &b.segs[0].table);
-        if (rc) return rc;
-    }
-    b.a_tc = p->d_atc;
+    TableHold hold(p);
+    int rc = hold.take(freq_hz);
+    if (rc) return rc;
+    b.segs[0].table = hold.idx;
+    b.segs[0].a_img = tc_image(p, hold.idx);
     const int nf = (int)(n_samples / kFrame);
     b.n_segs = 1;
     b.n_items = nf * kEw;
@@ -1140,11 +1217,11 @@ int bf_debug_stall(bf_plan_t p, const uint8_t* d_vin, int64_t wait_ns) {
     if (((uintptr_t)d_vin & 15) != 0) return fail(BF_EINVAL, "vin must be 16-byte aligned");
     CK(cudaSetDevice(p->device));
     Batch b = make_batch(p);
-    {
-        std::lock_guard<std::mutex> lk(p->mu);
-        int rc = table_for(p, 600e6, &b.segs[0].table);
-        if (rc) return rc;
-    }
+    TableHold hold(p);
+    int rc = hold.take(600e6);
+    if (rc) return rc;
+    b.segs[0].table = hold.idx;
+    b.segs[0].a_img = tc_image(p, hold.idx);
     b.n_segs = 1;
     b.n_items = kEw;                       // one frame, four E-W beams
     b.segs[0].vin = d_vin;
@@ -1156,6 +1233,18 @@ int bf_debug_stall(bf_plan_t p, const uint8_t* d_vin, int64_t wait_ns) {
         *(volatile int*)p->h_status = 0;
         return fail(BF_ETIMEDOUT, "a bounded device-side wait expired (expected in the stall check)");
     }
+    return BF_OK;
+}
+
+// ---- measurement aid ---------------------------------------------------------------------
+
+int bf_fp32_fma_probe(void* cuda_stream, int paired, int64_t iters, float* d_sink, int64_t n_sink, double* flop_out) {
+    if (iters <= 0 || !d_sink || n_sink < 256 || !flop_out) return fail(BF_EINVAL, "bad argument");
+    int dev = 0, sms = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    CK(fma_probe_launch(paired != 0, (long long)iters, d_sink, (long long)n_sink, sms, flop_out,
+                        (cudaStream_t)cuda_stream));
     return BF_OK;
 }
 

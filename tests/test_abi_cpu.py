@@ -66,6 +66,10 @@ def test_bad_geometry_rejected_before_cuda(built_lib):
     assert built_lib.bf_plan(ctypes.byref(c), ctypes.byref(ctypes.c_void_p())) == B.BF_EINVAL
     assert built_lib.bf_plan(None, None) == B.BF_EINVAL
     assert built_lib.bf_debug_tables(None, 600e6, None, None) == B.BF_EINVAL
+    for bad in (-1, 4097):                       # table slots: 0 (default 4096) or 1 .. 4096
+        c = B.bf_config_default(max_tables=bad)
+        assert built_lib.bf_plan(ctypes.byref(c), ctypes.byref(ctypes.c_void_p())) == B.BF_EINVAL
+        assert "max_tables" in B.bf_last_error()
 
 
 def test_null_plan_calls_fail_cleanly(built_lib):
