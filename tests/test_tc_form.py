@@ -8,7 +8,7 @@ output element against the oracle):
 
 * BF_TC_DFT256 (3 terms: twiddles hi+lo, data hi+lo): 1e-5, as the FP32 path;
 * BF_TC_DFT256_X2 (2 terms: twiddles hi, data hi+lo): 1e-3;
-* BF_TC_DFT256_X1 (1 term: twiddles hi, data hi): 5e-3 (stated after measurement).
+* BF_TC_DFT256_X1 (1 term: twiddles hi, data hi): 1e-3 (measured 3.3-3.5e-4).
 """
 import numpy as np
 import pytest
@@ -20,11 +20,12 @@ from paper_1702_04728_gb300 import synth
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-FORMS = {B.BF_TC_DFT256: 1e-5, B.BF_TC_DFT256_X2: 1e-3, B.BF_TC_DFT256_X1: 5e-3}
+FORMS = {B.BF_TC_DFT256: 1e-5, B.BF_TC_DFT256_X2: 1e-3, B.BF_TC_DFT256_X1: 1e-3}
 # GEMM stage, max |error| / rms over ~8e5 values: FP32 accumulation over K = 512
 # (3 terms); FP16 twiddle rounding 2^-12 summed over 256 random-phase feeds,
-# rms ~1.4e-4, ~5 sigma at the maximum (2 terms); plus FP16 data (1 term).
-GEMM_TOL = {B.BF_TC_DFT256: 2e-5, B.BF_TC_DFT256_X2: 1.5e-3, B.BF_TC_DFT256_X1: 3e-3}
+# rms ~1.4e-4, ~5 sigma at the maximum (2 terms); the FP16 data rounding adds
+# as much again (1 term, rms x sqrt 2).  Measured maxima 9.1e-6 / 6.5e-4 / 1.15e-3.
+GEMM_TOL = {B.BF_TC_DFT256: 2e-5, B.BF_TC_DFT256_X2: 1.5e-3, B.BF_TC_DFT256_X1: 2e-3}
 
 
 def dev(a):
