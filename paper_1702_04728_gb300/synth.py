@@ -295,3 +295,43 @@ def hash_noise_device(seed: int, n_chan: int, n_samples: int, device="cuda", sig
 
 
 SWEEP_FREQS = [400e6 + 6.25e6 * (i + 0.5) for i in range(64)]
+
+
+# --- device-side generator for band-wide workloads ------------------------------
+
+BAND_FREQS = [400e6 + CHAN_BW_HZ * (k + 0.5) for k in range(1024)]   # the 1024 coarse channels, 400-800 MHz
+
+
+def plane_wave_device(freqs_hz: Sequence[float], n_samples: int, seed: int,
+                      plane_waves: Iterable[PlaneWave] = (), sigma: float = 2.5,
+                      device="cuda", chunk_chan: int = 32):
+    """Packed voltages ``uint8[n_chan][n_samples][2048]`` generated on the device
+    with torch: noise N(0, sigma^2) per real part plus plane waves (same model as
+    ``make_voltages``: geometric phase per input, random per-sample phase per
+    polarisation), rounded half to even, clipped to +-7 and offset-encoded.
+    Deterministic in ``seed`` on a given device and torch build (torch's
+    generator, not numpy's: the host cannot rebuild the bytes, so tests copy
+    back the channels they check)."""
+    import torch
+    plane_waves = list(plane_waves)
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    out = torch.empty((len(freqs_hz), n_samples, N_INPUT), dtype=torch.uint8, device=device)
+    for c0 in range(0, len(freqs_hz), chunk_chan):
+        fs = list(freqs_hz[c0:c0 + chunk_chan])
+        nc = len(fs)
+        re = torch.randn((nc, n_samples, N_INPUT), generator=g, device=device) * sigma
+        im = torch.randn((nc, n_samples, N_INPUT), generator=g, device=device) * sigma
+        for p in plane_waves:
+            gain = np.stack([geometric_phase(f, p.u, p.s) * p.amplitude for f in fs])      # [nc, 2048]
+            gr = torch.from_numpy(gain.real.astype(np.float32)).to(device).view(nc, 1, N_CYL * N_FEED, N_POL)
+            gi = torch.from_numpy(gain.imag.astype(np.float32)).to(device).view(nc, 1, N_CYL * N_FEED, N_POL)
+            ph = torch.rand((nc, n_samples, 1, N_POL), generator=g, device=device) * (2.0 * math.pi)
+            cr, ci = torch.cos(ph), torch.sin(ph)
+            re += (gr * cr - gi * ci).view(nc, n_samples, N_INPUT)
+            im += (gr * ci + gi * cr).view(nc, n_samples, N_INPUT)
+        qr = torch.clamp(torch.round(re), -7, 7).to(torch.int16) + 8
+        qi = torch.clamp(torch.round(im), -7, 7).to(torch.int16) + 8
+        out[c0:c0 + nc] = ((qr << 4) | qi).to(torch.uint8)
+        del re, im, qr, qi
+    return out

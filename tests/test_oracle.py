@@ -310,6 +310,47 @@ def test_pointing_spacing_matches_fwhm_statements():
     assert abs(np.diff(th)[k] - t["low_elevation_fwhm_deg_approx"]) < 0.5
 
 
+def ns_response(freq, ns_sin, m, thetas_deg):
+    """|X[m]|^2 of the oracle's N-S stage for an exact unit plane wave from each
+    zenith angle (one time sample, one cylinder and polarisation)."""
+    s = np.sin(np.radians(np.asarray(thetas_deg, dtype=np.float64)))
+    n = np.arange(256)
+    x = np.exp(2j * np.pi * np.outer(s, n) * freq * O.CHIME.feed_spacing_m / O.C0)     # [angle, n]
+    x = x[:, None, :, None]                                                            # [T, c, n, p]
+    X = O.ns_beams(x, O.clamp_lut(freq, ns_sin))                                       # [T, c, p, m]
+    return np.abs(X[:, 0, 0, m]) ** 2
+
+
+def half_power_width(thetas, r):
+    k = int(np.argmax(r))
+    lo, hi = k, k
+    while lo > 0 and r[lo - 1] >= 0.5 * r[k]:
+        lo -= 1
+    while hi < len(r) - 1 and r[hi + 1] >= 0.5 * r[k]:
+        hi += 1
+    return thetas[hi] - thetas[lo]
+
+
+def test_beam_fwhm_matches_the_paper_at_the_bottom_of_the_band():
+    """Sec. 3.1: the formed N-S beams are ~0.5 deg wide (FWHM) at zenith and
+    up to ~2.8 deg at 10 deg elevation.  The widest beams are those at the
+    lowest frequency: at 400 MHz the oracle's beam toward zenith is 0.49 deg and
+    toward 80 deg zenith angle 2.8 deg wide; at 800 MHz half of that."""
+    ns = O.default_ns_sin().copy()
+    ns[128], ns[250] = 0.0, np.sin(np.radians(80.0))
+    f_lo, f_hi = 400e6 + 195312.5, 800e6 - 195312.5
+    th0 = np.linspace(-1.0, 1.0, 8001)
+    th80 = np.linspace(74.0, 86.0, 12001)
+    w0_lo = half_power_width(th0, ns_response(f_lo, ns, 128, th0))
+    w80_lo = half_power_width(th80, ns_response(f_lo, ns, 250, th80))
+    w0_hi = half_power_width(th0, ns_response(f_hi, ns, 128, th0))
+    assert abs(w0_lo - 0.5) < 0.05, w0_lo
+    assert abs(w80_lo - 2.8) < 0.25, w80_lo
+    assert abs(w0_hi / w0_lo - 0.5) < 0.02                       # the width scales as 1/f
+    # and as 1/cos(theta): 80 deg is 5.76 times wider than zenith
+    assert abs(w80_lo / w0_lo - 1.0 / np.cos(np.radians(80.0))) < 0.3
+
+
 # --- brute force on a tiny geometry -----------------------------------------------------
 
 TINY = O.Geometry(n_cyl=2, n_feed=4, n_pol=2, pad=2, n_ew=2, upchan=4, f_ds=2, t_ds=2,
