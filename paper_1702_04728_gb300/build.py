@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libchimebf.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["fused_fp32.cu", "fused_tc.cu", "post.cu", "runtime.cpp"]
+SOURCES = ["fused_fp32.cu", "fused_tc.cu", "fused_tc_pair.cu", "post.cu", "runtime.cpp"]
 
 
 def nvcc() -> str:

@@ -75,6 +75,9 @@ int fused_fp32_max_grid(int device);   // CTAs that fit at once (1 per SM)
 // 3 = stall check (1 term only): the MMA warp stays idle, so the producers'
 // bounded waits run out and the kernel reports through `status`.
 cudaError_t fused_tc_launch(const Batch& b, int terms, int mode, int grid, cudaStream_t s);
+// Tensor-core form, 1 term, detection: clusters of two CTAs (grid even, at most one
+// CTA per SM), each CTA 128 of the 256 bins of every item; no item is split.
+cudaError_t fused_tc_pair_launch(const Batch& b, int grid, cudaStream_t s);
 size_t tc_a_bytes(int terms);    // bytes of one table's twiddle image(s)
 cudaError_t skymap_launch(const float* in, int n_beams, long long per_beam, float* map, cudaStream_t s);
 cudaError_t dedisperse_launch(const float* in, const int* delays, int n_sub, long long nf, long long n_out,
@@ -88,7 +91,7 @@ cudaError_t rescale_u8_launch(const float* in, long long rows, long long nf, uin
                               cudaStream_t s);
 int tc_chunk_k(int terms);       // K elements per shared-memory chunk
 // FP32 FMA-pipe probe: 4 CTAs per SM (at most n_sink / 256) of 256 threads, each
-// thread `iters` (rounded up to 4) x 8 FFMA2 (paired) or 16 scalar FMA; *flop = flops issued.
+// thread `iters` (rounded up to 4) x 16 FFMA2 (paired) or 32 scalar FMA; *flop = flops issued.
 cudaError_t fma_probe_launch(bool paired, long long iters, float* sink, long long n_sink, int sms, double* flop,
                              cudaStream_t s);
 

@@ -411,5 +411,122 @@ __device__ __forceinline__ void upchan_pass2(uint32_t tlane, int hh, float (&acc
     }
 }
 
+// ---------------------------------------------------------------------------
+// the tensor-core forms' accumulator layout: lane = bin, columns [0, 128) = Re X(t),
+// [128, 256) = Im X(t) of block time t = 16 a + b
+// ---------------------------------------------------------------------------
+// TMEM access for the split Re/Im layout: 16 two-column loads (Re at base +
+// 16 a + b0, Im at base + 128 + 16 a + b0, a = 0..7) -> SoA pairs (b0, b0 + 1).
+__device__ __forceinline__ void tmem_ld_p1(uint32_t base, cp (&z)[8]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0, %1}, [%32];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%2, %3}, [%33];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%4, %5}, [%34];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%6, %7}, [%35];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%8, %9}, [%36];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%10, %11}, [%37];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%12, %13}, [%38];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%14, %15}, [%39];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%16, %17}, [%40];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%18, %19}, [%41];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%20, %21}, [%42];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%22, %23}, [%43];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%24, %25}, [%44];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%26, %27}, [%45];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%28, %29}, [%46];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%30, %31}, [%47];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(base), "r"(base + 16), "r"(base + 32), "r"(base + 48), "r"(base + 64), "r"(base + 80),
+          "r"(base + 96), "r"(base + 112), "r"(base + 128), "r"(base + 144), "r"(base + 160), "r"(base + 176),
+          "r"(base + 192), "r"(base + 208), "r"(base + 224), "r"(base + 240)
+        : "memory");
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+        z[a].re = make_float2(__uint_as_float(r[2 * a]), __uint_as_float(r[2 * a + 1]));
+        z[a].im = make_float2(__uint_as_float(r[16 + 2 * a]), __uint_as_float(r[16 + 2 * a + 1]));
+    }
+}
+
+__device__ __forceinline__ void tmem_st2(uint32_t taddr, float a, float b) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x2.b32 [%0], {%1, %2};"
+                 :: "r"(taddr), "r"(__float_as_uint(a)), "r"(__float_as_uint(b)) : "memory");
+}
+
+// 32 consecutive columns -> 32 floats
+__device__ __forceinline__ void tmem_ld32f(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// First up-channel pass in place on the split layout (t = 16 a + b): 8-point
+// DFT over a for the residue pair (b0, b0 + 1), twiddled by exp(-2 pi i b c / 128).
+__device__ __forceinline__ void upchan_pass1_split(uint32_t base, const float4* tw_s, int sub, int nsub) {
+#pragma unroll 1
+    for (int bp = sub; bp < 8; bp += nsub) {
+        const int b0 = 2 * bp;
+        cp z[8];
+        tmem_ld_p1(base + b0, z);
+        dft8(z);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            if (c) {
+                const float4 tw = tw_s[bp * 8 + c];
+                z[c] = cmulp(z[c], make_float2(tw.x, tw.y), make_float2(tw.z, tw.w));
+            }
+            tmem_st2(base + 16 * c + b0, z[c].re.x, z[c].re.y);
+            tmem_st2(base + 128 + 16 * c + b0, z[c].im.x, z[c].im.y);
+        }
+    }
+}
+
+// Second pass on the split layout: Re of (c, b) at 16 c + b, Im at 128 + 16 c + b.
+__device__ __forceinline__ void upchan_pass2_split(uint32_t base, float2 (&acc)[kSub], float2* dump, int sub,
+                                                   int nsub) {
+#pragma unroll 1
+    for (int cpi = sub; cpi < 4; cpi += nsub) {
+        float re[32], im[32];
+        tmem_ld32f(base + 32 * cpi, re);
+        tmem_ld32f(base + 128 + 32 * cpi, im);
+        cp y[16];
+#pragma unroll
+        for (int b = 0; b < 16; ++b) {
+            y[b].re = make_float2(re[b], re[16 + b]);
+            y[b].im = make_float2(im[b], im[16 + b]);
+        }
+        dft16(y);
+        if (dump) {
+#pragma unroll
+            for (int dd = 0; dd < 16; ++dd) {
+                const int c0 = 2 * cpi;
+                dump[(c0 + 8 * dd + kUp / 2) & (kUp - 1)] = make_float2(y[dd].re.x, y[dd].im.x);
+                dump[(c0 + 1 + 8 * dd + kUp / 2) & (kUp - 1)] = make_float2(y[dd].re.y, y[dd].im.y);
+            }
+        } else {
+#pragma unroll
+            for (int dd = 0; dd < 16; ++dd) {
+                const float2 p = fma2(y[dd].im, y[dd].im, mul2(y[dd].re, y[dd].re));
+                acc[(dd + 8) & 15] = add2(acc[(dd + 8) & 15], p);
+            }
+        }
+    }
+}
+
 }  // namespace
 }  // namespace chimebf

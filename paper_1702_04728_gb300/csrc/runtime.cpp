@@ -610,10 +610,15 @@ int launch_jobs(bf_plan_s* p, std::vector<Job>& jobs, size_t bytes) {
         bb.epoch = ++p->launches;
         // a launch of at most half a grid of items runs every item as two halves on two CTAs
         // (the 2-term tensor-core form never splits)
-        int grid = std::min(p->grid, bb.n_items);
-        if (p->terms != 2 && 2 * bb.n_items <= p->grid) grid = 2 * bb.n_items;
-        cudaError_t e = p->terms ? fused_tc_launch(bb, p->terms, 0, grid, p->stream)
-                                 : fused_fp32_launch(bb, grid, p->stream);
+        cudaError_t e;
+        if (p->terms == 1) {
+            // the 1-term form runs on CTA pairs, one item per pair at a time
+            e = fused_tc_pair_launch(bb, 2 * std::min(p->grid / 2, bb.n_items), p->stream);
+        } else {
+            int grid = std::min(p->grid, bb.n_items);
+            if (p->terms != 2 && 2 * bb.n_items <= p->grid) grid = 2 * bb.n_items;
+            e = p->terms ? fused_tc_launch(bb, p->terms, 0, grid, p->stream) : fused_fp32_launch(bb, grid, p->stream);
+        }
         if (e != cudaSuccess) return cuda_fail(e, "fused kernel launch");
     }
     for (auto& c : carries) {
