@@ -40,7 +40,11 @@ BYTES_PER_SAMPLE = 1.0 + 1024 * 16 * 4 / (384 * 2048)   # 1 B in + float32 out
 KERNEL_SOURCES = {
     "fused_fp32_kernel": ["fused_fp32.cu", "device_common.cuh", "bf_internal.h"],
     "fused_tc_kernel": ["fused_tc.cu", "device_common.cuh", "bf_internal.h"],
+    "fused_tc_pair_kernel": ["fused_tc_pair.cu", "device_common.cuh", "bf_internal.h"],
 }
+# the kernel that runs each form's detecting launches
+FORM_KERNEL = {"fp32_fft": "fused_fp32_kernel", "tc_dft256_3term": "fused_tc_kernel",
+               "tc_dft256_2term": "fused_tc_kernel", "tc_dft256_1term": "fused_tc_pair_kernel"}
 
 
 def kernel_hash(kernel: str) -> str:
@@ -52,9 +56,10 @@ def kernel_hash(kernel: str) -> str:
     return h.hexdigest()
 
 
-def recorded_traffic(kernel: str, form: str):
+def recorded_traffic(form: str):
     """DRAM bytes per launch from the committed ncu summary, if the kernel's
     sources are unchanged since the capture (else None)."""
+    kernel = FORM_KERNEL[form]
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             rec = json.load(f)[form]
@@ -145,9 +150,9 @@ def make_input(rank: int, world: int = 1):
     return raw, freqs
 
 
-def fp32_peak(B, torch, stream, iters=65536, reps=10):
+def fp32_peak(B, torch, stream, iters=32768, reps=10):
     """Measured throughput of the FP32 FMA pipe (TFLOP/s): the library's FFMA2
-    probe (4 CTAs per SM, 8 independent chains per thread), device-timed on
+    probe (4 CTAs per SM, 16 independent chains per thread), device-timed on
     `stream` after warm-up, with the SM clock sampled meanwhile; the scalar-FMA
     probe beside it."""
     n_sink = 4 * torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count * 256
@@ -168,14 +173,15 @@ def fp32_peak(B, torch, stream, iters=65536, reps=10):
     return res
 
 
-def sweep_run(B, torch, stream, ws, steps=3):
+def sweep_run(B, torch, stream, ws, roofline, steps=3):
     """64 channels over 400-800 MHz x 390625 samples (1 s) x 2048 inputs = 51.2 GB,
-    counter-based noise generated on the device; device-timed per form."""
+    counter-based noise with five dispersed bursts (DM 100-2000) generated on the
+    device; device-timed per form."""
     from paper_1702_04728_gb300 import synth
     n_chan, T = 64, 390625
-    vin = synth.hash_noise_device(11, n_chan, T)
+    vin = synth.hash_noise_device(11, n_chan, T, offsets=synth.burst_offsets(synth.SWEEP_FREQS, T, synth.SWEEP_BURSTS, 11))
     out = torch.empty(1024, 16 * n_chan, T // 384, dtype=torch.float32, device="cuda")
-    res = {"workload": "64 ch (400-800 MHz) x 390625 samples x 2048 inputs (51.2 GB), noise only",
+    res = {"workload": "64 ch (400-800 MHz) x 390625 samples x 2048 inputs (51.2 GB), noise and 5 bursts (DM 100-2000)",
            "forms": []}
     for fid, fname in [(B.BF_FP32_FFT, "fp32_fft"), (B.BF_TC_DFT256_X1, "tc_dft256_1term")]:
         p = B.Plan(stream=stream, form=fid)
@@ -192,7 +198,8 @@ def sweep_run(B, torch, stream, ws, steps=3):
         p.close()
         ms = e0.elapsed_time(e1) / steps
         res["forms"].append({"form": fname, "ms_per_step": ms,
-                             "input_samples_per_s": n_chan * T * N_INPUT / (ms * 1e-3)})
+                             "input_samples_per_s": n_chan * T * N_INPUT / (ms * 1e-3),
+                             "roofline": roofline(fname, n_chan * T * N_INPUT, ms)})
     del vin, out
     torch.cuda.empty_cache()
     return res
@@ -380,7 +387,6 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    peaks, peak_kind = load_peaks()
     form_names = {B.BF_FP32_FFT: "fp32_fft", B.BF_TC_DFT256: "tc_dft256_3term",
                   B.BF_TC_DFT256_X2: "tc_dft256_2term", B.BF_TC_DFT256_X1: "tc_dft256_1term"}
     headline_form = getattr(B, args.form)
@@ -404,6 +410,33 @@ def main():
     with ClockSampler(local) as clk_probe:
         probe = fp32_peak(B, torch, stream)
     probe["clocks"] = clk_probe.summary()
+    peaks, peak_kind = load_peaks()
+    n_sm_dev = torch.cuda.get_device_properties(local).multi_processor_count
+    form_terms = {"fp32_fft": 0, "tc_dft256_3term": 3, "tc_dft256_2term": 2, "tc_dft256_1term": 1}
+
+    def roofline(fname, n_samples, ms_):
+        """Roofline of one form's launch: the tensor pipe (2048 GEMM flop per input-sample
+        and term) for the tensor-core forms, the FP32 pipe (162 algorithmic flop per
+        input-sample) for the FFT form, against the measured peaks."""
+        terms_ = form_terms[fname]
+        if terms_:
+            achieved = 2048.0 * terms_ * n_samples / (ms_ * 1e-3) / 1e12
+            pk = peaks.get("bf16_tflops", 1927.5)
+            return {"bound": "tensor", "achieved": achieved, "peak": pk, "unit": "TFLOP/s", "frac": achieved / pk,
+                    "traffic": recorded_traffic(fname),
+                    "peak_note": f"dense FP16 tensor peak = measured bf16 burst ({peak_kind}; FP16 and BF16 "
+                                 f"share the rate); achieved = 2048 x {terms_} GEMM flop per input-sample"}
+        nominal = n_sm_dev * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        alu_peak = probe["ffma2"]["tflops"]
+        achieved = FLOP_PER_SAMPLE * n_samples / (ms_ * 1e-3) / 1e12
+        return {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                "frac": achieved / alu_peak, "traffic": recorded_traffic(fname),
+                "peak_note": f"FP32 FMA pipe, measured: the FFMA2 probe (4 CTAs/SM x 256 threads x 16 "
+                             f"independent chains) at a median SM clock of {probe['clocks'].get('sm_mhz')} MHz; "
+                             f"nominal {n_sm_dev} SMs x 128 lanes x 2 flop x "
+                             f"{peaks.get('sm_max_mhz', 2070.0):.0f} MHz = {nominal:.1f}; "
+                             f"achieved = {FLOP_PER_SAMPLE:.0f} algorithmic flop per input-sample",
+                "frac_of_nominal": achieved / nominal}
 
     # products of the output (sky map, 8-bit rescale, dedispersion), device-timed
     def timed(fn, reps=20):
@@ -453,14 +486,9 @@ def main():
             fp.poll(t)
         fms = e0.elapsed_time(e1) / nrep
         fp.close()
-        terms = {B.BF_TC_DFT256: 3, B.BF_TC_DFT256_X2: 2, B.BF_TC_DFT256_X1: 1}.get(fid, 0)
         samples_ = N_CHAN * N_SAMP * N_INPUT
-        run = {"form": fname, "ms_per_step": fms, "input_samples_per_s": samples_ / (fms * 1e-3)}
-        if terms:
-            tflops = 2048.0 * terms * samples_ / (fms * 1e-3) / 1e12
-            run["tensor_tflops"] = tflops
-            run["tensor_frac_of_measured_bf16_dense"] = tflops / peaks.get("bf16_tflops", 1927.5)
-            run["tensor_flop_per_sample"] = 2048 * terms
+        run = {"form": fname, "ms_per_step": fms, "input_samples_per_s": samples_ / (fms * 1e-3),
+               "roofline": roofline(fname, samples_, fms)}
         form_runs.append(run)
         form_outs[fname] = fo[:, :, :16].cpu().numpy()
 
@@ -539,25 +567,7 @@ def main():
         hbm_gbs = BYTES_PER_SAMPLE * samples / (ms * 1e-3) / 1e9
         fname = form_names[headline_form]
         terms = {B.BF_TC_DFT256: 3, B.BF_TC_DFT256_X2: 2, B.BF_TC_DFT256_X1: 1}.get(headline_form, 0)
-        if terms:
-            achieved = 2048.0 * terms * samples / (ms * 1e-3) / 1e12
-            roof = {"bound": "tensor", "achieved": achieved, "peak": peaks.get("bf16_tflops", 1927.5),
-                    "unit": "TFLOP/s", "frac": achieved / peaks.get("bf16_tflops", 1927.5),
-                    "traffic": recorded_traffic("fused_tc_kernel", fname),
-                    "peak_note": f"dense FP16 tensor peak = measured bf16 burst ({peak_kind}; FP16 and BF16 "
-                                 f"share the rate); achieved = 2048 x {terms} GEMM flop per input-sample"}
-        else:
-            nominal = n_sm * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-            alu_peak = probe["ffma2"]["tflops"]
-            achieved = FLOP_PER_SAMPLE * samples / (ms * 1e-3) / 1e12
-            roof = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
-                    "frac": achieved / alu_peak, "traffic": recorded_traffic("fused_fp32_kernel", fname),
-                    "peak_note": f"FP32 FMA pipe, measured: the FFMA2 probe (4 CTAs/SM x 256 threads x 8 "
-                                 f"independent chains) at a median SM clock of {probe['clocks'].get('sm_mhz')} MHz; "
-                                 f"nominal {n_sm} SMs x 128 lanes x 2 flop x "
-                                 f"{peaks.get('sm_max_mhz', 2070.0):.0f} MHz = {nominal:.1f}; "
-                                 f"achieved = {FLOP_PER_SAMPLE:.0f} algorithmic flop per input-sample",
-                    "frac_of_nominal": achieved / nominal}
+        roof = roofline(fname, samples, ms)
         line = {
             "metric": METRIC, "value": value, "unit": "input-samples/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
@@ -582,7 +592,7 @@ def main():
             "fp32_probe": probe,
         }
         if args.sweep:
-            line["sweep"] = sweep_run(B, torch, stream, ws)
+            line["sweep"] = sweep_run(B, torch, stream, ws, roofline)
         if args.serving_seconds > 0:
             cap = samples / (ms * 1e-3)
             line["serving"] = [serving_run(B, torch, cap, ld, args.serving_seconds, form=headline_form)

@@ -281,7 +281,7 @@ int bf_debug_upchan(bf_plan_t p, double freq_hz, const uint8_t* d_vin, int64_t n
  * enqueues on cuda_stream (cudaStream_t; NULL = the legacy default stream) one
  * kernel of 4 CTAs per SM (at most n_sink / 256 CTAs) x 256 threads on the
  * current device; each thread runs iters (rounded up to a multiple of 4) steps
- * of 8 independent packed FFMA2 chains (paired != 0) or 16 scalar FFMA chains,
+ * of 16 independent packed FFMA2 chains (paired != 0) or 32 scalar FFMA chains,
  * so the pipe and not latency sets the rate.  d_sink: device float [n_sink],
  * n_sink >= 256, caller-owned, receives one value per thread.  *flop_out = the
  * flops the kernel issues (2 per FMA); the caller times the launch on its

@@ -157,7 +157,7 @@ __device__ __align__(256) int g_dd_delays[kDdStaticMaxSub];
 // chains converge to c / (1 - b) and stay finite; their sum is stored so that
 // no FMA can be removed.
 constexpr int kProbeThreads = 256;
-constexpr int kProbeChains = 8;
+constexpr int kProbeChains = 16;
 
 template <bool kPair>
 __global__ void __launch_bounds__(kProbeThreads) fma_probe_kernel(long long iters, float* __restrict__ sink) {
