@@ -247,28 +247,44 @@ def _mix_np(x: np.ndarray) -> np.ndarray:
 
 
 def hash_noise_rows(seed: int, chan: int, n_samples_per_chan: int, t0: int, t1: int,
-                    sigma: float = 2.5) -> np.ndarray:
-    """Host copy of rows [t0, t1) of channel `chan`: uint8 [t1 - t0][2048]."""
-    thr = np.array(noise_thresholds(sigma), dtype=np.uint64)
+                    sigma: float = 2.5, offsets=None) -> np.ndarray:
+    """Host copy of rows [t0, t1) of channel `chan`: uint8 [t1 - t0][2048].
+    offsets: optional (re, im) int8 [n_chan][n_samples] burst offsets in units
+    of 1/BURST_Q count (see burst_offsets); row t of the channel is quantised
+    with the thresholds of its offset."""
     base = (np.uint64(seed) << np.uint64(40)) + np.uint64(chan * n_samples_per_chan * N_INPUT)
     idx = base + np.arange(t0 * N_INPUT, t1 * N_INPUT, dtype=np.uint64)
-    z = _mix_np(idx)
+    z = _mix_np(idx).reshape(t1 - t0, N_INPUT)
     lo = z & np.uint64(0xFFFFFFFF)
     hi = z >> np.uint64(32)
-    re = -7 + (hi[:, None] >= thr[None, :]).sum(axis=1).astype(np.int16)
-    im = -7 + (lo[:, None] >= thr[None, :]).sum(axis=1).astype(np.int16)
+    if offsets is None:
+        thr = np.array(noise_thresholds(sigma), dtype=np.uint64)
+        re = -7 + (hi[..., None] >= thr).sum(axis=-1).astype(np.int16)
+        im = -7 + (lo[..., None] >= thr).sum(axis=-1).astype(np.int16)
+    else:
+        table = burst_thresholds(sigma)                                   # [2 R + 1][14]
+        t_re = table[offsets[0][chan, t0:t1].astype(np.int64) + BURST_R]   # [rows][14]
+        t_im = table[offsets[1][chan, t0:t1].astype(np.int64) + BURST_R]
+        re = -7 + (hi[..., None] >= t_re[:, None, :]).sum(axis=-1).astype(np.int16)
+        im = -7 + (lo[..., None] >= t_im[:, None, :]).sum(axis=-1).astype(np.int16)
     return encode(re, im).reshape(t1 - t0, N_INPUT)
 
 
 def hash_noise_device(seed: int, n_chan: int, n_samples: int, device="cuda", sigma: float = 2.5,
-                      chunk: int = 1 << 26):
-    """Device generation of uint8 [n_chan][n_samples][2048] (same bytes as above)."""
+                      chunk: int = 1 << 26, offsets=None):
+    """Device generation of uint8 [n_chan][n_samples][2048] (same bytes as above);
+    offsets as in hash_noise_rows.  chunk: bytes per step, a multiple of 2048."""
     import torch
+    assert chunk % N_INPUT == 0
     thr = noise_thresholds(sigma)
     out = torch.empty(n_chan * n_samples * N_INPUT, dtype=torch.uint8, device=device)
     total = out.numel()
     base = seed << 40
     mask32 = 0xFFFFFFFF
+    if offsets is not None:
+        table = torch.from_numpy(burst_thresholds(sigma).astype(np.int64)).to(device)     # [2 R + 1][14]
+        off_re = torch.from_numpy(np.ascontiguousarray(offsets[0]).reshape(-1).astype(np.int64) + BURST_R).to(device)
+        off_im = torch.from_numpy(np.ascontiguousarray(offsets[1]).reshape(-1).astype(np.int64) + BURST_R).to(device)
 
     def as_i64(v):                                   # uint64 constant as a wrapped int64
         return v - (1 << 64) if v >= (1 << 63) else v
@@ -282,19 +298,83 @@ def hash_noise_device(seed: int, n_chan: int, n_samples: int, device="cuda", sig
         z = (z ^ srl(z, 30)) * as_i64(_SM_M1)
         z = (z ^ srl(z, 27)) * as_i64(_SM_M2)
         z = z ^ srl(z, 31)
-        hi = srl(z, 32)
-        lo = z & mask32
-        re = torch.zeros(n, dtype=torch.int16, device=device)
-        im = torch.zeros(n, dtype=torch.int16, device=device)
-        for t in thr:
-            re += (hi >= t).to(torch.int16)
-            im += (lo >= t).to(torch.int16)
-        out[s:s + n] = (((re + 1) << 4) | (im + 1)).to(torch.uint8)   # (v + 8) with v = count - 7
+        hi = srl(z, 32).view(-1, N_INPUT)
+        lo = (z & mask32).view(-1, N_INPUT)
+        re = torch.zeros_like(hi, dtype=torch.int16)
+        im = torch.zeros_like(hi, dtype=torch.int16)
+        if offsets is None:
+            for t in thr:
+                re += (hi >= t).to(torch.int16)
+                im += (lo >= t).to(torch.int16)
+        else:
+            rows = torch.arange(s // N_INPUT, (s + n) // N_INPUT, device=device)     # global row = chan * T + t
+            t_re = table[off_re[rows]]                                                # [rows][14]
+            t_im = table[off_im[rows]]
+            for k in range(len(thr)):
+                re += (hi >= t_re[:, k:k + 1]).to(torch.int16)
+                im += (lo >= t_im[:, k:k + 1]).to(torch.int16)
+        out[s:s + n] = (((re + 1) << 4) | (im + 1)).to(torch.uint8).view(-1)   # (v + 8) with v = count - 7
         del z, hi, lo, re, im
     return out.view(n_chan, n_samples, N_INPUT)
 
 
+# --- dispersed bursts in the counter-based workload ------------------------------
+#
+# A burst from zenith (u = s = 0) reaches every input of a channel with the same
+# complex amplitude b(t); the sample is then clip(round(noise + b)).  b is
+# quantised to BURST_Q steps per count (at most BURST_R steps) on the host in
+# FP64, and the rounding of noise + b becomes a comparison of the same uniform
+# integer with shifted thresholds floor(2^32 Phi((k + 1/2 - b) / sigma)), one
+# table row per quantised b (row BURST_R, b = 0, holds the plain noise
+# thresholds).  Host and device use the same table and integer comparisons, so
+# they still agree bit for bit.
+
+BURST_Q = 256
+BURST_R = 127
+
+
+def burst_thresholds(sigma: float = 2.5, clip: int = 7) -> np.ndarray:
+    """uint64 [2 BURST_R + 1][2 clip]: thresholds for offsets b = (i - BURST_R) / BURST_Q."""
+    from math import erf, sqrt
+    out = np.empty((2 * BURST_R + 1, 2 * clip), dtype=np.uint64)
+    for i in range(2 * BURST_R + 1):
+        b = (i - BURST_R) / BURST_Q
+        for kk, k in enumerate(range(-clip, clip)):
+            cdf = 0.5 * (1.0 + erf((k + 0.5 - b) / (sigma * sqrt(2.0))))
+            out[i, kk] = min(2**32 - 1, int(cdf * 2**32))
+    return out
+
+
+def burst_offsets(freqs_hz: Sequence[float], n_samples: int, bursts: Iterable[Burst], seed: int):
+    """(re, im) int8 [n_chan][n_samples]: the bursts' complex amplitude per channel
+    and sample (burst_series: Gaussian envelope, complex-Gaussian carrier,
+    arrival k_DM DM (f^-2 - f_ref^-2), intra-channel chirp) in units of
+    1/BURST_Q count, rounded and clipped to +-BURST_R.  Channels the burst does
+    not reach inside the window are left at zero."""
+    bursts = list(bursts)
+    re = np.zeros((len(freqs_hz), n_samples), np.int8)
+    im = np.zeros((len(freqs_hz), n_samples), np.int8)
+    T = n_samples * DT_S
+    for bi, b in enumerate(bursts):
+        for ci, f in enumerate(freqs_hz):
+            arrive = b.t0_s + K_DM * b.dm * ((f / 1e6) ** -2 - (b.f_ref_hz / 1e6) ** -2)
+            smear = 8.3e-6 * b.dm * (CHAN_BW_HZ / 1e6) / (f / 1e9) ** 3 + 5 * b.fwhm_s
+            if arrive + smear < 0 or arrive - smear > T:
+                continue
+            rng = np.random.default_rng([seed, bi, ci])
+            x = burst_series(b, f, n_samples, rng)
+            re[ci] = np.clip(np.rint(re[ci] + x.real * BURST_Q), -BURST_R, BURST_R).astype(np.int8)
+            im[ci] = np.clip(np.rint(im[ci] + x.imag * BURST_Q), -BURST_R, BURST_R).astype(np.int8)
+    return re, im
+
+
 SWEEP_FREQS = [400e6 + 6.25e6 * (i + 0.5) for i in range(64)]
+# the sweep's five bursts: zenith, 1 ms FWHM, nominal S/N 200 over the 64 channels (0.07 counts
+# per input, well below the noise), reaching 800 MHz 10 + 20 i ms into the 1 s window and
+# sweeping down the band (a DM-100 burst crosses 48 of the 64 channels inside the window, a
+# DM-2000 burst 5)
+SWEEP_BURSTS = [Burst(burst_amplitude(64, snr=200.0), u=0.0, s=0.0, dm=dm, t0_s=0.01 + 0.02 * i, f_ref_hz=800e6)
+                for i, dm in enumerate((100.0, 300.0, 700.0, 1200.0, 2000.0))]
 
 
 # --- device-side generator for band-wide workloads ------------------------------

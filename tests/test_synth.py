@@ -31,3 +31,30 @@ def test_hash_noise_distribution():
 def test_encode_rejects_out_of_range():
     with pytest.raises(ValueError):
         synth.encode(np.array([8]), np.array([0]))
+
+
+def test_burst_offsets_host_equals_device_on_cpu():
+    rng = np.random.default_rng(1)
+    off = (rng.integers(-127, 128, size=(3, 50)).astype(np.int8), rng.integers(-127, 128, size=(3, 50)).astype(np.int8))
+    dev = synth.hash_noise_device(5, 3, 50, device="cpu", chunk=1 << 12, offsets=off).numpy()
+    for ch in range(3):
+        assert np.array_equal(synth.hash_noise_rows(5, ch, 50, 0, 50, offsets=off), dev[ch])
+    zero = (np.zeros((3, 50), np.int8), np.zeros((3, 50), np.int8))
+    assert np.array_equal(synth.hash_noise_device(5, 3, 50, device="cpu", chunk=1 << 12, offsets=zero).numpy(),
+                          synth.hash_noise_device(5, 3, 50, device="cpu", chunk=1 << 12).numpy())
+    # row BURST_R of the table is the plain noise threshold set
+    assert synth.burst_thresholds()[synth.BURST_R].tolist() == synth.noise_thresholds()
+
+
+def test_burst_offset_shifts_the_quantised_mean():
+    """A constant offset b moves the mean of clip(round(N(0, 2.5^2) + b)) by b
+    (to first order: the clip at +-7 is 2.8 sigma away)."""
+    n = 200000
+    b = 40                                                   # 40 / 256 count
+    off = (np.full((1, n // 2048 + 1), b, np.int8), np.zeros((1, n // 2048 + 1), np.int8))
+    x = synth.hash_noise_rows(3, 0, n // 2048 + 1, 0, n // 2048 + 1, offsets=off)
+    re = (x >> 4).astype(float) - 8
+    im = (x & 15).astype(float) - 8
+    se = np.sqrt(synth.quantized_noise_variance() / re.size)
+    assert abs(re.mean() - b / synth.BURST_Q) < 5 * se + 0.002
+    assert abs(im.mean()) < 5 * se
