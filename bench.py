@@ -31,6 +31,15 @@ sys.path.insert(0, ROOT)
 
 METRIC = "beamformed input-samples/s & HBM roofline %, FFT vs TC-DFT at stated err; p99 latency"
 WORKLOAD = "node_slice: 4 ch (410/520/650/790 MHz) x 49152 samples x 2048 inputs, DM-500 burst"
+FORM_NAMES = {"BF_FP32_FFT": "fp32_fft", "BF_TC_DFT256": "tc_dft256_3term",
+              "BF_TC_DFT256_X2": "tc_dft256_2term", "BF_TC_DFT256_X1": "tc_dft256_1term"}
+
+
+def bench_config(form: str) -> dict:
+    """The workload both arms report (static: no measured values)."""
+    return {"workload": WORKLOAD, "n_chan": N_CHAN, "n_samples": N_SAMP, "n_inputs": N_INPUT,
+            "form": FORM_NAMES[form], "output": "float32 [1024][64][128]",
+            "l2": "inputs (402.7 MB) larger than L2; no flush"}
 N_CHAN, N_SAMP, N_INPUT = 4, 49152, 2048
 FLOP_PER_SAMPLE = 162.0          # N-S 90 (5 N log2 N at N = 512 per 256 inputs) + E-W 32 + up-channel 35 + detect 5
 BYTES_PER_SAMPLE = 1.0 + 1024 * 16 * 4 / (384 * 2048)   # 1 B in + float32 out
@@ -312,27 +321,28 @@ def oracle_one_core(raw, freqs, frames_per_chan: int = 1):
 
 
 def run_reference(args):
+    """The oracle as it stands on the host cores: W untimed and K timed steps, each
+    one frame (384 samples) of every channel of the node slice, so that the run
+    ends within minutes at the default step counts."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return
     raw, freqs = make_input(0, 1)
-    # each step is a bounded sample (3 frames of each channel) so the run ends in minutes
-    steps = max(1, min(args.steps, 5))
-    vals = []
-    cpu_baseline(raw, freqs, frames_per_chan=1)          # warm-up (BLAS threads, caches)
+    for _ in range(args.warmup):
+        cb = cpu_baseline(raw, freqs, frames_per_chan=1)
     t_all = time.perf_counter()
-    cb = None
-    for _ in range(steps):
-        cb = cpu_baseline(raw, freqs, frames_per_chan=3)
-        vals.append(cb["value"])
+    for _ in range(args.steps):
+        cb = cpu_baseline(raw, freqs, frames_per_chan=1)
     dt = time.perf_counter() - t_all
-    v = statistics.median(vals)
+    v = args.steps * N_CHAN * 384 * N_INPUT / dt
+    sample = (f"per step the first frame (384 samples) of each of the {N_CHAN} channels, numpy FP64 "
+              f"direct DFTs, {1e3 * dt / args.steps:.0f} ms")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "input-samples/s", "n_gpus": 1,
-            "steps": len(vals), "warmup": 1, "ms_per_step": 1e3 * dt / len(vals), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample": cb["sample"]},
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": bench_config(args.form),
             "cpu_baseline": {"value": v, "unit": "input-samples/s", "cores": cb["cores"], "kind": "oracle",
-                             "sample": cb["sample"]},
+                             "sample": sample},
             "e2e": {"value": v, "unit": "input-samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -387,8 +397,7 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    form_names = {B.BF_FP32_FFT: "fp32_fft", B.BF_TC_DFT256: "tc_dft256_3term",
-                  B.BF_TC_DFT256_X2: "tc_dft256_2term", B.BF_TC_DFT256_X1: "tc_dft256_1term"}
+    form_names = {getattr(B, k): v for k, v in FORM_NAMES.items()}
     headline_form = getattr(B, args.form)
     if headline_form != B.BF_FP32_FFT:
         plan.close()
@@ -552,6 +561,16 @@ def main():
         e2e_step()
     barrier()
     e2e_ms = (time.perf_counter() - t0) * 1e3 / args.e2e_steps
+    # this box's pinned host -> device copy rate: one copy of the whole input, device-timed
+    c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for i in range(4):
+        if i == 1:
+            c0.record(copy_s)
+        with torch.cuda.stream(copy_s):
+            vin.copy_(host_in, non_blocking=True)
+    c1.record(copy_s)
+    copy_s.synchronize()
+    h2d_ms = c0.elapsed_time(c1) / 3
     host_out = torch.cat([torch.cat([host_outs_p[(c, k)] for k in range(len(sched[c]))], dim=2)
                           for c in range(N_CHAN)], dim=1)
 
@@ -573,14 +592,13 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f16-tc/f32" if terms else "f32",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n_chan": N_CHAN, "n_samples": N_SAMP, "n_inputs": N_INPUT,
-                       "form": fname, "output": "float32 [1024][64][128]",
-                       "l2": "inputs (402.7 MB) larger than L2; no flush",
-                       "hbm_gbs": hbm_gbs, "hbm_frac_of_measured": hbm_gbs / peaks["hbm_gbs"]},
+            "config": bench_config(args.form),
+            "hbm": {"gbs": hbm_gbs, "frac_of_measured": hbm_gbs / peaks["hbm_gbs"]},
             "roofline": roof,
             "e2e": {"value": samples * ws / (e2e_ms * 1e-3), "unit": "input-samples/s",
                     "h2d_bytes_per_step": samples, "d2h_bytes_per_step": out.numel() * 4,
-                    "ms_per_step": e2e_ms, "how": f"wall clock; requests of {wave} frames (one wave of "
+                    "ms_per_step": e2e_ms, "h2d_copy_ms": h2d_ms,
+                    "h2d_copy_GBps": samples / (h2d_ms * 1e-3) / 1e9, "how": f"wall clock; requests of {wave} frames (one wave of "
                                                   "work items) per channel on one stream, a short first and "
                                                   "last piece, H2D of the next piece overlapping beamforming "
                                                   "of the previous one, channels alternating between two "
