@@ -32,7 +32,12 @@ sys.path.insert(0, ROOT)
 METRIC = "beamformed input-samples/s & HBM roofline %, FFT vs TC-DFT at stated err; p99 latency"
 WORKLOAD = "node_slice: 4 ch (410/520/650/790 MHz) x 49152 samples x 2048 inputs, DM-500 burst"
 FORM_NAMES = {"BF_FP32_FFT": "fp32_fft", "BF_TC_DFT256": "tc_dft256_3term",
-              "BF_TC_DFT256_X2": "tc_dft256_2term", "BF_TC_DFT256_X1": "tc_dft256_1term"}
+              "BF_TC_DFT256_X2": "tc_dft256_2term", "BF_TC_DFT256_X1": "tc_dft256_1term",
+              "BF_TC_DFT512": "tc_dft512_1term"}
+# tensor flop per input-sample of each tensor-core form: 8 real flop per (row, feed) and
+# term, over the 256 clamped rows or all 512 rows of the zero-padded transform
+TC_FLOP = {"tc_dft256_3term": 3 * 2048, "tc_dft256_2term": 2 * 2048, "tc_dft256_1term": 2048,
+           "tc_dft512_1term": 4096}
 
 
 def bench_config(form: str) -> dict:
@@ -53,7 +58,8 @@ KERNEL_SOURCES = {
 }
 # the kernel that runs each form's detecting launches
 FORM_KERNEL = {"fp32_fft": "fused_fp32_kernel", "tc_dft256_3term": "fused_tc_kernel",
-               "tc_dft256_2term": "fused_tc_kernel", "tc_dft256_1term": "fused_tc_pair_kernel"}
+               "tc_dft256_2term": "fused_tc_kernel", "tc_dft256_1term": "fused_tc_pair_kernel",
+               "tc_dft512_1term": "fused_tc_pair_kernel"}
 
 
 def kernel_hash(kernel: str) -> str:
@@ -238,6 +244,7 @@ def serving_run(B, torch, capacity_sps, load, seconds, n_streams=200, seed=0, fo
     import queue as _queue
     pend = _queue.Queue()
     lat = []
+    parts = {"queue": [], "stream_wait": [], "batch_exec": [], "collect": [], "done": []}
 
     def poller():                       # completions arrive in batch order; poll FIFO
         while True:
@@ -245,8 +252,14 @@ def serving_run(B, torch, capacity_sps, load, seconds, n_streams=200, seed=0, fo
             if item is None:
                 return
             t, ts = item
-            plan.poll(t)
+            _, _, tm = plan.poll_timed(t)
             lat.append(time.perf_counter() - ts)
+            # the runtime's timeline of the request: queued, on the GPU, waiting to be collected
+            parts["queue"].append(tm[1] - tm[0])
+            parts["stream_wait"].append(max(0.0, tm[2] - tm[1] - tm[4]))
+            parts["batch_exec"].append(tm[4])
+            parts["collect"].append(tm[3] - tm[2])
+            parts["done"].append(tm[2] - tm[0])
 
     th = threading.Thread(target=poller, daemon=True)
     th.start()
@@ -273,8 +286,17 @@ def serving_run(B, torch, capacity_sps, load, seconds, n_streams=200, seed=0, fo
     plan.close()
     lat.sort()
     pct = lambda q: 1e3 * lat[min(len(lat) - 1, int(q * len(lat)))]
+
+    def pcts(v):
+        v = sorted(v)
+        return {"p50_ms": 1e3 * v[len(v) // 2], "p99_ms": 1e3 * v[min(len(v) - 1, int(0.99 * len(v)))]}
     return {"offered_load_frac": load, "offered_input_GBps": load * capacity_sps / 1e9,
             "requests": len(lat), "p50_ms": pct(0.50), "p99_ms": pct(0.99), "max_ms": 1e3 * lat[-1],
+            "breakdown": {k: pcts(v) for k, v in parts.items() if v},
+            "breakdown_note": "runtime timeline per request: queue = submit to its batch's launch, "
+                              "stream_wait = launch to completion seen minus batch_exec (earlier batches still "
+                              "on the stream), batch_exec = the batch's device time (CUDA events), collect = "
+                              "completion to this poller's FIFO collection, done = submit to completion seen",
             "sustained_samples_per_s": samples / elapsed, "streams": n_streams, "seconds": seconds}
 
 
@@ -358,7 +380,7 @@ def main():
     ap.add_argument("--serving-seconds", type=float, default=2.0)
     ap.add_argument("--sweep", type=int, default=1, help="time the 64-channel x 1 s sweep (0: skip)")
     ap.add_argument("--form", default="BF_FP32_FFT",
-                    choices=["BF_FP32_FFT", "BF_TC_DFT256", "BF_TC_DFT256_X2", "BF_TC_DFT256_X1"])
+                    choices=list(FORM_NAMES))
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
@@ -421,20 +443,18 @@ def main():
     probe["clocks"] = clk_probe.summary()
     peaks, peak_kind = load_peaks()
     n_sm_dev = torch.cuda.get_device_properties(local).multi_processor_count
-    form_terms = {"fp32_fft": 0, "tc_dft256_3term": 3, "tc_dft256_2term": 2, "tc_dft256_1term": 1}
 
     def roofline(fname, n_samples, ms_):
         """Roofline of one form's launch: the tensor pipe (2048 GEMM flop per input-sample
         and term) for the tensor-core forms, the FP32 pipe (162 algorithmic flop per
         input-sample) for the FFT form, against the measured peaks."""
-        terms_ = form_terms[fname]
-        if terms_:
-            achieved = 2048.0 * terms_ * n_samples / (ms_ * 1e-3) / 1e12
+        if fname in TC_FLOP:
+            achieved = TC_FLOP[fname] * n_samples / (ms_ * 1e-3) / 1e12
             pk = peaks.get("bf16_tflops", 1927.5)
             return {"bound": "tensor", "achieved": achieved, "peak": pk, "unit": "TFLOP/s", "frac": achieved / pk,
                     "traffic": recorded_traffic(fname),
                     "peak_note": f"dense FP16 tensor peak = measured bf16 burst ({peak_kind}; FP16 and BF16 "
-                                 f"share the rate); achieved = 2048 x {terms_} GEMM flop per input-sample"}
+                                 f"share the rate); achieved = {TC_FLOP[fname]} GEMM flop per input-sample"}
         nominal = n_sm_dev * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
         alu_peak = probe["ffma2"]["tflops"]
         achieved = FLOP_PER_SAMPLE * n_samples / (ms_ * 1e-3) / 1e12
@@ -585,7 +605,7 @@ def main():
         n_sm = torch.cuda.get_device_properties(local).multi_processor_count
         hbm_gbs = BYTES_PER_SAMPLE * samples / (ms * 1e-3) / 1e9
         fname = form_names[headline_form]
-        terms = {B.BF_TC_DFT256: 3, B.BF_TC_DFT256_X2: 2, B.BF_TC_DFT256_X1: 1}.get(headline_form, 0)
+        terms = fname in TC_FLOP
         roof = roofline(fname, samples, ms)
         line = {
             "metric": METRIC, "value": value, "unit": "input-samples/s", "n_gpus": ws,

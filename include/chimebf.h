@@ -44,13 +44,18 @@ extern "C" {
 #define BF_ENOTICKET  -5   /* unknown, already collected or cancelled ticket        */
 #define BF_ESHUTDOWN  -6   /* plan is being destroyed                               */
 
-/* N-S transform forms (bf_config.form).  The tensor-core forms evaluate the
- * clamped zero-padded FFT as the equivalent DFT over the 256 kept rows on
- * tcgen05 (FP16 operands, FP32 accumulation); the E-W phased feed line is split
- * into FP16 hi + lo, the twiddles are FP16 hi (+ lo). */
+/* N-S transform forms (bf_config.form).  The BF_TC_DFT256* forms evaluate the
+ * clamped zero-padded FFT (Sec. 3.1, Eq. 1) as the equivalent DFT over the 256
+ * kept rows on tcgen05 (FP16 operands, FP32 accumulation); the E-W phased feed
+ * line is split into FP16 hi + lo, the twiddles are FP16 hi (+ lo).
+ * BF_TC_DFT512 evaluates all 512 rows of the zero-padded transform (the 512
+ * redundant beams of Sec. 3.1) with one GEMM term and applies the clamp to the
+ * result: the same output as BF_TC_DFT256_X1 at twice the GEMM and
+ * up-channelisation work.  Its plans refuse the stage dumps and the stall
+ * check (BF_EINVAL). */
 #define BF_FP32_FFT      0 /* FP32 zero-padded FFT on the CUDA cores                */
 #define BF_TC_DFT256     1 /* 3 GEMM terms: twiddles hi+lo x data hi+lo             */
-#define BF_TC_DFT512     2 /* all 512 padded rows (same result as 256; not built)   */
+#define BF_TC_DFT512     2 /* all 512 padded rows, 1 GEMM term, clamp at the output */
 #define BF_TC_DFT256_X2  3 /* 2 GEMM terms: twiddles hi x data hi+lo                */
 #define BF_TC_DFT256_X1  4 /* 1 GEMM term: twiddles hi x data hi                    */
 
@@ -87,7 +92,7 @@ typedef struct {
                                NULL for (m - 127.5)/128; copied by bf_plan        */
     const double* ew_sin;   /* host [n_ew] sin of the E-W beam angles, or NULL for
                                sin({-0.6, -0.2, 0.2, 0.6} deg); copied            */
-    int form;               /* BF_FP32_FFT or a BF_TC_DFT256* form                */
+    int form;               /* BF_FP32_FFT, a BF_TC_DFT256* form or BF_TC_DFT512  */
     int mode;               /* BF_MODE_DIRECT | BF_MODE_SERVING                   */
     size_t mem_budget;      /* serving admission budget in bytes (0 = unlimited)  */
     int max_streams;        /* distinct stream_ids held at once (0 = 1024)        */
@@ -158,6 +163,23 @@ int bf_submit(bf_plan_t p, const bf_request* r, uint64_t* ticket);
  * BF_PENDING: still running.  Negative: error (the ticket is released).
  */
 int bf_poll(bf_plan_t p, uint64_t ticket, int64_t timeout_us, int64_t* n_frames_out);
+
+/*
+ * bf_poll plus the request's timeline, for latency breakdowns of a serving
+ * plan (no counterpart in the paper).  When the call collects the ticket (BF_OK
+ * or an error), times (host array of 5 doubles) receives, in seconds on the
+ * host's monotonic clock: [0] bf_submit accepted the request; [1] its batch's
+ * kernels were enqueued; [2] the runtime saw the batch's completion event (the
+ * plan thread checks every 20 us while batches run, and every poll checks);
+ * [3] this call collected it; and [4] the batch's device time, from CUDA
+ * events recorded on the plan's stream before its first and after its last
+ * operation (0 if the batch failed).  So [1] - [0] is the wait in the queue,
+ * [2] - [1] - [4] the wait behind earlier batches on the stream (plus launch
+ * and event latency), [4] the batch itself, [3] - [2] the caller's delay in
+ * collecting.  On BF_PENDING times is left unchanged.  A null times is
+ * BF_EINVAL.
+ */
+int bf_poll_timed(bf_plan_t p, uint64_t ticket, int64_t timeout_us, int64_t* n_frames_out, double* times);
 
 /* Drain outstanding work, free all plan-owned memory and the plan thread. */
 int bf_destroy(bf_plan_t p);

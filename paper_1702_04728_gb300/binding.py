@@ -24,7 +24,8 @@ N_BEAMS, N_SUB, FRAME, N_INPUT = 1024, 16, 384, 2048
 
 SYMBOLS = ["bf_config_default", "bf_plan", "bf_frames_out", "bf_submit", "bf_poll", "bf_destroy",
            "bf_last_error", "bf_skymap", "bf_rescale_u8", "bf_dedisperse", "bf_debug_tables", "bf_debug_gather_order", "bf_debug_gemm", "bf_debug_unpack", "bf_debug_beams",
-           "bf_debug_upchan", "bf_debug_stall", "bf_dedisperse_static", "bf_fp32_fma_probe"]
+           "bf_debug_upchan", "bf_debug_stall", "bf_dedisperse_static", "bf_fp32_fma_probe",
+           "bf_poll_timed"]
 
 
 class BfError(RuntimeError):
@@ -69,6 +70,7 @@ def lib() -> ctypes.CDLL:
         L.bf_frames_out.argtypes = [P, U64, I64, ctypes.POINTER(I64)]
         L.bf_submit.argtypes = [P, ctypes.POINTER(bf_request), ctypes.POINTER(U64)]
         L.bf_poll.argtypes = [P, U64, I64, ctypes.POINTER(I64)]
+        L.bf_poll_timed.argtypes = [P, U64, I64, ctypes.POINTER(I64), ctypes.POINTER(D)]
         L.bf_destroy.argtypes = [P]
         L.bf_last_error.argtypes = []
         L.bf_last_error.restype = ctypes.c_char_p
@@ -181,6 +183,16 @@ def bf_poll(plan: int, ticket: int, timeout_us: int = -1):
     return rc, nf.value
 
 
+def bf_poll_timed(plan: int, ticket: int, timeout_us: int = -1):
+    """Returns (status, n_frames_out, times): times = (submitted, launched, completion
+    seen, collected) in seconds on the host's monotonic clock and the batch's device
+    time in seconds, None while pending."""
+    nf = ctypes.c_int64()
+    times = (ctypes.c_double * 5)()
+    rc = _check(lib().bf_poll_timed(plan, ticket, timeout_us, ctypes.byref(nf), times))
+    return rc, nf.value, (tuple(times) if rc == BF_OK else None)
+
+
 def bf_destroy(plan: int) -> None:
     _check(lib().bf_destroy(plan))
 
@@ -286,6 +298,9 @@ class Plan:
 
     def poll(self, ticket: int, timeout_us: int = -1):
         return bf_poll(self.handle, ticket, timeout_us)
+
+    def poll_timed(self, ticket: int, timeout_us: int = -1):
+        return bf_poll_timed(self.handle, ticket, timeout_us)
 
     def run(self, vin, freqs, stream_id: int = 0, flags: int = BF_END_OF_STREAM, ew_sin_frames=None):
         """vin: torch.uint8 CUDA tensor [n_chan, T, 2048] -> float32 [1024, 16 n_chan, n_frames]."""

@@ -21,6 +21,7 @@ constexpr int kSub = kUp / kFds; // 16 sub-channels
 constexpr int kFrame = kUp * kTds;   // 384 samples per frame
 constexpr int kInput = kCyl * kFeed * kPol;   // 2048 bytes per time sample
 constexpr int kBeams = kEw * kNs;    // 1024 intensity beams
+constexpr int kInvLen = kBins + kNs;  // per table: first beam of each bin, next beam of each beam
 
 // Segments per launch (kernel-parameter space holds the descriptors).
 constexpr int kMaxSegs = 160;
@@ -48,6 +49,8 @@ struct Batch {
     int n_segs;
     int n_items;
     const int16_t* lut;      // [n_tables][256]   clamp table, Eq. (1)
+    const int16_t* inv;      // [n_tables][kInvLen] 512-row form: first beam of each bin, then the
+                             // next beam with the same bin (-1 ends a list)
     const int16_t* order;    // [n_tables][256]   FP32 form: beam taken by consumer slot (TMEM lane + 128 x half)
     const float2* ew;        // [n_tables][4 ew][4 cyl] E-W phases
     const float2* tw512;     // [512] exp(-2 pi i e / 512)
@@ -78,6 +81,9 @@ cudaError_t fused_tc_launch(const Batch& b, int terms, int mode, int grid, cudaS
 // Tensor-core form, 1 term, detection: clusters of two CTAs (grid even, at most one
 // CTA per SM), each CTA 128 of the 256 bins of every item; no item is split.
 cudaError_t fused_tc_pair_launch(const Batch& b, int grid, cudaStream_t s);
+// The 512-row form (all bins of the zero-padded transform, clamp at the output) on clusters
+// of four CTAs; the grid is the clusters that fit at once.
+cudaError_t fused_tc_dft512_launch(const Batch& b, cudaStream_t s);
 size_t tc_a_bytes(int terms);    // bytes of one table's twiddle image(s)
 cudaError_t skymap_launch(const float* in, int n_beams, long long per_beam, float* map, cudaStream_t s);
 cudaError_t dedisperse_launch(const float* in, const int* delays, int n_sub, long long nf, long long n_out,

@@ -1,31 +1,41 @@
-// Tensor-core form, 1 term, on CTA pairs (arXiv 1702.04728, Sec. 3 and Sec. 3.1).
+// Tensor-core forms with 1 term on clusters of R CTAs (arXiv 1702.04728, Sec. 3
+// and Sec. 3.1).
 //
-// The N-S stage is the DFT over the 256 clamped rows of the zero-padded FFT
-// (Eq. 1), evaluated on tcgen05 as X[m][t] = sum_k A[m][k] B[k][t] with
-// A[m][2n] = cos, A[m][2n+1] = sin (2 pi n L(m) / 512) and B holding the E-W
-// phased feed line y_j of block time t as (yr, yi) in column t and (yi, -yr)
-// in column 128 + t (FP16 operands, FP32 accumulation; one term: A and B
-// rounded to FP16 once).
+// The N-S stage is a DFT over rows of the zero-padded 512-point transform,
+// evaluated on tcgen05 as X[m][t] = sum_k A[m][k] B[k][t] with A[m][2n] = cos,
+// A[m][2n+1] = sin (2 pi n k_m / 512) and B holding the E-W phased feed line
+// y_j of block time t as (yr, yi) in column t and (yi, -yr) in column 128 + t
+// (FP16 operands, FP32 accumulation; one term: A and B rounded to FP16 once).
+//   * R = 2 (BF_TC_DFT256_X1): the rows are the 256 clamped bins k_m = L(m)
+//     of Eq. (1), one per N-S beam, so TMEM lane m of the pair is beam m;
+//   * R = 4 (BF_TC_DFT512): the rows are all 512 bins k_m = m, the full
+//     zero-padded transform (the 512 redundant beams of Sec. 3.1, twice the
+//     GEMM and up-channel work), and the clamp of Eq. (1) is applied at the
+//     output: bin k goes to every beam m with L(m) = k (none, one, or several
+//     where aliasing maps pointings to one bin).
 //
-// A cluster of two CTAs owns a work item (channel segment, frame F, E-W beam
-// j) and its six passes (3 blocks x 2 pols).  CTA r takes the bins m = 128 r
-// .. 128 r + 127:
+// A cluster of R CTAs owns a work item (channel segment, frame F, E-W beam
+// j) and its six passes (3 blocks x 2 pols).  CTA r takes the rows
+// 128 r .. 128 r + 127:
 //   * its 128 rows of A for all K (128 KB) stay resident in shared memory,
-//     reloaded only when the item's channel changes;
-//   * each CTA builds half of every B chunk (block times 64 r .. 64 r + 63:
-//     unpack, E-W toward beam j, FP16) into its own shared memory and sends
-//     that half to the partner with one CTA-to-CTA bulk copy, so both hold the
-//     whole chunk and each issues M = 128 MMAs on its own bins;
+//     reloaded only when the item's channel changes (R = 2; the 512-row
+//     matrix does not depend on the frequency);
+//   * each CTA builds 1/R of every B chunk (block times (128/R) r ..
+//     (128/R)(r + 1) - 1: unpack, E-W toward beam j, FP16) into its own
+//     shared memory and sends that part to the other CTAs with CTA-to-CTA
+//     bulk copies, so every CTA holds the whole chunk and issues M = 128 MMAs
+//     on its own rows;
 //   * the accumulator of a pass is 128 bins x 256 columns, half of tensor
 //     memory, so two passes alternate between the halves: the MMAs of pass
 //     p + 1 overlap the up-channel passes (Sec. 3.2) of pass p.
-// Warps: 0-7 build B (one (time, feed octet) task per thread and chunk, the raw
-// words of the next chunk prefetched into registers), 8-11 (one per
-// tensor-memory lane quarter) run the up-channel passes and detection for one
-// bin each, warp 12 issues the MMAs and the A copies.  Hand-offs are mbarriers
-// (and one named barrier among the builders); every wait is bounded by
-// %globaltimer, and on expiry the CTA records the failure and leaves its loops
-// (its partner's waits then expire too).
+// Warps: 0-7 build B (one (time, feed octet) task per thread and chunk for
+// R = 2, half an octet for R = 4; the raw words of the next chunk prefetched
+// into registers), 8-11 (one per tensor-memory lane quarter) run the
+// up-channel passes and detection for one row each, warp 12 issues the MMAs
+// and the A copies.  Hand-offs are mbarriers (and one named barrier among the
+// builders); every wait is bounded by %globaltimer, and on expiry the CTA
+// records the failure and leaves its loops (the other CTAs' waits then expire
+// too).
 #include "device_common.cuh"
 
 #include <cuda_fp16.h>
@@ -41,10 +51,14 @@ constexpr int kQNCH = 2 * kFeed / kQKC;           // 8 chunks per pass
 constexpr int kQSBO = kQKC / 8 * 128;             // 1024 bytes between 8-row groups of an operand
 constexpr int kQAChunk = 128 * kQKC * 2;          // 16 KB: this CTA's 128 rows of A for one chunk
 constexpr int kQBStage = 256 * kQKC * 2;          // 32 KB: one B chunk (N = 256)
-constexpr int kQBPart = 8 * kQSBO;                // 8 KB: 64 consecutive N rows of a chunk
+// B rows built by one CTA of an R-CTA cluster, and the bytes of one of its two blocks
+// (rows t and 128 + t)
+template <int R>
+constexpr int kQRows = 128 / R;
+template <int R>
+constexpr int kQPart = kQRows<R> / 8 * kQSBO;     // 8 KB (R = 2), 4 KB (R = 4)
 constexpr int kQNB = 2;                           // B ring stages
 constexpr int kQBuild = 8;                        // builder warps (a multiple of 4)
-constexpr int kQTasks = 8 / kQBuild;              // (time, octet) tasks per builder thread and chunk
 constexpr int kQUp = 4;                           // up-channel warps
 constexpr int kQThreads = 32 * (kQBuild + kQUp + 1);
 constexpr int kQMmaWarp = kQBuild + kQUp;
@@ -77,9 +91,10 @@ __device__ __forceinline__ void qmma(uint32_t dtmem, uint64_t adesc, uint64_t bd
         : "memory");
 }
 
-// commit of this thread's outstanding MMAs to the same mbarrier in both CTAs of the pair
-__device__ __forceinline__ void qcommit_both(uint32_t mbar) {
-    const uint16_t mask = 3;
+// commit of this thread's outstanding MMAs to the same mbarrier in every CTA of the cluster
+template <int R>
+__device__ __forceinline__ void qcommit_all(uint32_t mbar) {
+    const uint16_t mask = (uint16_t)((1u << R) - 1u);
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;"
                  :: "r"(mbar), "h"(mask) : "memory");
 }
@@ -107,7 +122,7 @@ __device__ __forceinline__ uint32_t n_clusters() {
     return r;
 }
 
-// the partner CTA's shared-memory address of a local one
+// another CTA's shared-memory address of a local one
 __device__ __forceinline__ uint32_t peer_addr(uint32_t a, uint32_t peer) {
     uint32_t r;
     asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(peer));
@@ -128,8 +143,8 @@ __device__ __forceinline__ void q_g2s(uint32_t dst, const void* src, uint32_t by
                  :: "r"(dst), "l"(src), "r"(bytes), "r"(mbar) : "memory");
 }
 
-// bulk copy this CTA's shared memory -> the partner's (both addresses shared::cluster
-// for the destination), completing on the partner's mbarrier
+// bulk copy this CTA's shared memory -> another CTA's (destination and its mbarrier
+// as shared::cluster addresses), completing on that CTA's mbarrier
 __device__ __forceinline__ void q_s2peer(uint32_t dst_cluster, uint32_t src_cta, uint32_t bytes,
                                          uint32_t mbar_cluster) {
     asm volatile("cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
@@ -155,71 +170,110 @@ __device__ __forceinline__ uint32_t qh2u(__half2 h) { return *reinterpret_cast<u
 // k-groups 128 B apart, 8-row groups kQSBO apart.
 __device__ __forceinline__ int qoff(int r, int kg) { return (r >> 3) * kQSBO + kg * 128 + (r & 7) * 16; }
 
-// A builder thread's two tasks (block time t, feed octet) of a chunk: lanes 0-7 take 8
-// consecutive times and lane bits 3-4 the octet, so each warp load instruction reads
-// whole 32-byte sectors and each quarter warp stores one 128-byte core matrix.
-__device__ __forceinline__ void q_task(uint32_t rank, int bt_id, int i, int& t, int& oct) {
+// A builder thread's task of a chunk: block time t, feed octet `oct` and, for R = 4,
+// which half of the octet (feeds 4 half .. 4 half + 3; R = 2 takes both halves).
+// R = 2: lanes 0-7 take 8 consecutive times and lane bits 3-4 the octet; R = 4: lanes
+// 0-7 the times, lane bit 3 the half, lane bit 4 and warp bit 0 the octet, so in both
+// each warp load instruction reads whole 32-byte sectors.
+template <int R>
+__device__ __forceinline__ void q_task(uint32_t rank, int bt_id, int& t, int& oct, int& half) {
     const int lane = bt_id & 31, warp = bt_id >> 5;
-    oct = (lane >> 3) & 3;
-    t = 64 * (int)rank + (lane & 7) + 8 * (warp + kQBuild * i);
+    if constexpr (R == 2) {
+        oct = (lane >> 3) & 3;
+        half = 0;
+        t = 64 * (int)rank + (lane & 7) + 8 * warp;
+    } else {
+        half = (lane >> 3) & 1;
+        oct = ((warp & 1) << 1) | ((lane >> 4) & 1);
+        t = 32 * (int)rank + (lane & 7) + 8 * (warp >> 1);
+    }
 }
 
-struct QRaw {
-    uint4 v[kQTasks][kCyl];
+template <int R>
+struct QRaw;
+template <>
+struct QRaw<2> {
+    uint4 v[kCyl];
+};
+template <>
+struct QRaw<4> {
+    uint2 v[kCyl];
 };
 
-__device__ __forceinline__ void q_load(const Seg& sg, long long row0, int kc, uint32_t rank, int bt_id, QRaw& r) {
+template <int R>
+__device__ __forceinline__ void q_load(const Seg& sg, long long row0, int kc, uint32_t rank, int bt_id, QRaw<R>& r) {
+    int t, oct, half;
+    q_task<R>(rank, bt_id, t, oct, half);
+    const uint8_t* rp = frame_row(sg, row0 + t) + 2 * ((kQKC / 2) * kc + 8 * oct) + 8 * half;
 #pragma unroll
-    for (int i = 0; i < kQTasks; ++i) {
-        int t, oct;
-        q_task(rank, bt_id, i, t, oct);
-        const uint8_t* rp = frame_row(sg, row0 + t) + 2 * ((kQKC / 2) * kc + 8 * oct);
-#pragma unroll
-        for (int c = 0; c < kCyl; ++c) r.v[i][c] = __ldg(reinterpret_cast<const uint4*>(rp + c * (kFeed * kPol)));
+    for (int c = 0; c < kCyl; ++c) {
+        if constexpr (R == 2)
+            r.v[c] = __ldg(reinterpret_cast<const uint4*>(rp + c * (kFeed * kPol)));
+        else
+            r.v[c] = __ldg(reinterpret_cast<const uint2*>(rp + c * (kFeed * kPol)));
     }
 }
 
-// unpack, E-W toward beam j, FP16; row t = (yr, yi) per feed, row 128 + t = (yi, -yr)
-__device__ __forceinline__ void q_build(const QRaw& r, uint32_t sel, const EwW& w, unsigned char* stage, uint32_t rank,
-                                        int bt_id) {
+// unpack, E-W toward beam j, FP16 of feeds 4 h .. 4 h + 3 of an octet from the raw words
+// (w0[c], w1[c]); row t = (yr, yi) per feed, row 128 + t = (yi, -yr)
+__device__ __forceinline__ void q_build_half(const uint32_t (&w0)[kCyl], const uint32_t (&w1)[kCyl], uint32_t sel,
+                                             const EwW& w, unsigned char* stage, int t, int kg) {
+    cp y0, y1;                                    // SoA: (n, n + 2) and (n + 1, n + 3)
 #pragma unroll
-    for (int i = 0; i < kQTasks; ++i) {
-        int t, oct;
-        q_task(rank, bt_id, i, t, oct);
-#pragma unroll
-        for (int half = 0; half < 2; ++half) {           // feeds 4 half .. 4 half + 3 of the octet
-            cp y0, y1;                                    // SoA: (n, n + 2) and (n + 1, n + 3)
-#pragma unroll
-            for (int c = 0; c < kCyl; ++c) {
-                const uint32_t w0 = half ? r.v[i][c].z : r.v[i][c].x, w1 = half ? r.v[i][c].w : r.v[i][c].y;
-                const uint32_t g0 = __byte_perm(w0, 0u, sel), g1 = __byte_perm(w1, 0u, sel);
-                const float2 xi0 = nib2<0>(g0, g1), xr0 = nib2<1>(g0, g1);
-                const float2 xi1 = nib2<2>(g0, g1), xr1 = nib2<3>(g0, g1);
-                if (c == 0) {
-                    y0 = {xr0, xi0};
-                    y1 = {xr1, xi1};
-                } else {
-                    y0.re = fma2(xi0, w.NI[c - 1], fma2(xr0, w.R[c - 1], y0.re));
-                    y0.im = fma2(xr0, w.I[c - 1], fma2(xi0, w.R[c - 1], y0.im));
-                    y1.re = fma2(xi1, w.NI[c - 1], fma2(xr1, w.R[c - 1], y1.re));
-                    y1.im = fma2(xr1, w.I[c - 1], fma2(xi1, w.R[c - 1], y1.im));
-                }
-            }
-            const float yr[4] = {y0.re.x, y1.re.x, y0.re.y, y1.re.y};
-            const float yi[4] = {y0.im.x, y1.im.x, y0.im.y, y1.im.y};
-            uint32_t vre[4], vim[4];
-#pragma unroll
-            for (int f = 0; f < 4; ++f) {
-                vre[f] = qh2u(__floats2half2_rn(yr[f], yi[f]));
-                vim[f] = qh2u(__floats2half2_rn(yi[f], -yr[f]));
-            }
-            const int kg = 2 * oct + half;
-            *reinterpret_cast<uint4*>(stage + qoff(t, kg)) = make_uint4(vre[0], vre[1], vre[2], vre[3]);
-            *reinterpret_cast<uint4*>(stage + qoff(128 + t, kg)) = make_uint4(vim[0], vim[1], vim[2], vim[3]);
+    for (int c = 0; c < kCyl; ++c) {
+        const uint32_t g0 = __byte_perm(w0[c], 0u, sel), g1 = __byte_perm(w1[c], 0u, sel);
+        const float2 xi0 = nib2<0>(g0, g1), xr0 = nib2<1>(g0, g1);
+        const float2 xi1 = nib2<2>(g0, g1), xr1 = nib2<3>(g0, g1);
+        if (c == 0) {
+            y0 = {xr0, xi0};
+            y1 = {xr1, xi1};
+        } else {
+            y0.re = fma2(xi0, w.NI[c - 1], fma2(xr0, w.R[c - 1], y0.re));
+            y0.im = fma2(xr0, w.I[c - 1], fma2(xi0, w.R[c - 1], y0.im));
+            y1.re = fma2(xi1, w.NI[c - 1], fma2(xr1, w.R[c - 1], y1.re));
+            y1.im = fma2(xr1, w.I[c - 1], fma2(xi1, w.R[c - 1], y1.im));
         }
     }
+    const float yr[4] = {y0.re.x, y1.re.x, y0.re.y, y1.re.y};
+    const float yi[4] = {y0.im.x, y1.im.x, y0.im.y, y1.im.y};
+    uint32_t vre[4], vim[4];
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+        vre[f] = qh2u(__floats2half2_rn(yr[f], yi[f]));
+        vim[f] = qh2u(__floats2half2_rn(yi[f], -yr[f]));
+    }
+    *reinterpret_cast<uint4*>(stage + qoff(t, kg)) = make_uint4(vre[0], vre[1], vre[2], vre[3]);
+    *reinterpret_cast<uint4*>(stage + qoff(128 + t, kg)) = make_uint4(vim[0], vim[1], vim[2], vim[3]);
 }
 
+template <int R>
+__device__ __forceinline__ void q_build(const QRaw<R>& r, uint32_t sel, const EwW& w, unsigned char* stage,
+                                        uint32_t rank, int bt_id) {
+    int t, oct, half;
+    q_task<R>(rank, bt_id, t, oct, half);
+    if constexpr (R == 2) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            uint32_t w0[kCyl], w1[kCyl];
+#pragma unroll
+            for (int c = 0; c < kCyl; ++c) {
+                w0[c] = h ? r.v[c].z : r.v[c].x;
+                w1[c] = h ? r.v[c].w : r.v[c].y;
+            }
+            q_build_half(w0, w1, sel, w, stage, t, 2 * oct + h);
+        }
+    } else {
+        uint32_t w0[kCyl], w1[kCyl];
+#pragma unroll
+        for (int c = 0; c < kCyl; ++c) {
+            w0[c] = r.v[c].x;
+            w1[c] = r.v[c].y;
+        }
+        q_build_half(w0, w1, sel, w, stage, t, 2 * oct + half);
+    }
+}
+
+template <int R>
 __global__ void __launch_bounds__(kQThreads, 1) fused_tc_pair_kernel(const __grid_constant__ Batch bt) {
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ uint32_t tmem_base_s;
@@ -230,11 +284,11 @@ __global__ void __launch_bounds__(kQThreads, 1) fused_tc_pair_kernel(const __gri
     uint64_t* mbar_s = reinterpret_cast<uint64_t*>(reinterpret_cast<unsigned char*>(tw_s) + kQSmemTw);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const uint32_t rank = cluster_rank(), peer = rank ^ 1u;
+    const uint32_t rank = cluster_rank();
     const uint32_t smem0 = static_cast<uint32_t>(__cvta_generic_to_shared(smem));
     const uint32_t bar0 = static_cast<uint32_t>(__cvta_generic_to_shared(&mbar_s[0]));
-    auto bfull = [&](int s) { return bar0 + 8u * (uint32_t)s; };               // 1 local arrive + the partner's 16 KB
-    auto bempty = [&](int s) { return bar0 + 8u * (uint32_t)(kQNB + s); };     // both CTAs' MMA commits
+    auto bfull = [&](int s) { return bar0 + 8u * (uint32_t)s; };               // 1 local arrive + the others' parts
+    auto bempty = [&](int s) { return bar0 + 8u * (uint32_t)(kQNB + s); };     // every CTA's MMA commit
     auto accfull = [&](int b) { return bar0 + 8u * (uint32_t)(2 * kQNB + b); }; // last commit of a pass
     auto tfree = [&](int b) { return bar0 + 8u * (uint32_t)(2 * kQNB + 2 + b); }; // the up-channel warps
     const uint32_t afull = bar0 + 8u * (uint32_t)(2 * kQNB + 4), adone = afull + 8u;
@@ -247,7 +301,7 @@ __global__ void __launch_bounds__(kQThreads, 1) fused_tc_pair_kernel(const __gri
     if (tid == 0) {
         for (int i = 0; i < kQNB; ++i) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(bfull(i)) : "memory");
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 2;" :: "r"(bempty(i)) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(bempty(i)), "n"(R) : "memory");
         }
         for (int i = 0; i < 2; ++i) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(accfull(i)) : "memory");
@@ -266,7 +320,7 @@ __global__ void __launch_bounds__(kQThreads, 1) fused_tc_pair_kernel(const __gri
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    cluster_sync();                        // both CTAs' barriers exist before any remote arrival
+    cluster_sync();                        // every CTA's barriers exist before any remote arrival
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_base_s;
     constexpr int PASSES = kTds * kPol;
@@ -297,7 +351,7 @@ __global__ void __launch_bounds__(kQThreads, 1) fused_tc_pair_kernel(const __gri
                     q_expect(afull, (uint32_t)kQSmemA);
 #pragma unroll 1
                     for (int kc = 0; kc < kQNCH; ++kc)
-                        q_g2s(smem0 + (uint32_t)(kc * kQAChunk), a_img + (size_t)kc * (2 * kQAChunk) + rank * kQAChunk,
+                        q_g2s(smem0 + (uint32_t)(kc * kQAChunk), a_img + (size_t)kc * (R * kQAChunk) + rank * kQAChunk,
                               (uint32_t)kQAChunk, afull);
                     if (!mbar_wait(afull, p_afull, wlim)) ok = false;
                     p_afull ^= 1u;
@@ -322,7 +376,7 @@ __global__ void __launch_bounds__(kQThreads, 1) fused_tc_pair_kernel(const __gri
                         for (int ks = 0; ks < kQKC / 16; ++ks)
                             qmma(tmem + 256u * (uint32_t)buf, qdesc(a0 + ks * 256), qdesc(b0 + ks * 256),
                                  (kc | ks) ? 1u : 0u);
-                        qcommit_both(bempty(s));
+                        qcommit_all<R>(bempty(s));
                         if (kc == kQNCH - 1) qcommit(accfull(buf));
                         if (abort_s) ok = false;
                     }
@@ -350,27 +404,27 @@ __global__ void __launch_bounds__(kQThreads, 1) fused_tc_pair_kernel(const __gri
             const int F = local >> 2, j = local & 3;
             EwW w;
             load_ew_frame(sg, bt.ew, F, j, w);
-            QRaw raw;
-            q_load(sg, (long long)F * kFrame, 0, rank, bt_id, raw);
+            QRaw<R> raw;
+            q_load<R>(sg, (long long)F * kFrame, 0, rank, bt_id, raw);
             for (int ps = 0; ps < PASSES && ok; ++ps) {
                 const int blk = ps >> 1, pol = ps & 1;
                 const uint32_t sel = 0x4400u | ((2u + pol) << 4) | (uint32_t)pol;
                 for (int kc = 0; kc < kQNCH && ok; ++kc, ++c) {
                     const int s = (int)(c % kQNB);
                     if (c >= kQNB) {
-                        // both CTAs' MMAs have read stage s (chunk c - kQNB), and with them the
-                        // partner's copy out of it
+                        // every CTA's MMAs have read stage s (chunk c - kQNB), and with them the
+                        // copies out of it into the other CTAs
                         if (!mbar_wait(bempty(s), (p_bempty >> s) & 1u, wlim)) ok = false;
                         p_bempty ^= 1u << s;
                     }
-                    QRaw cur = raw;
+                    QRaw<R> cur = raw;
                     const bool last = kc + 1 == kQNCH;
                     if (!last || ps + 1 < PASSES) {
                         const int nblk = last ? ((ps + 1) >> 1) : blk;
-                        q_load(sg, (long long)F * kFrame + nblk * kUp, last ? 0 : kc + 1, rank, bt_id, raw);
+                        q_load<R>(sg, (long long)F * kFrame + nblk * kUp, last ? 0 : kc + 1, rank, bt_id, raw);
                     }
                     unsigned char* stage = b_ring + s * kQBStage;
-                    q_build(cur, sel, w, stage, rank, bt_id);
+                    q_build<R>(cur, sel, w, stage, rank, bt_id);
                     // the generic-proxy stores are visible to the tensor core and the bulk copy
                     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                     // all builders have written their part; they stop together (an expired wait
@@ -382,12 +436,17 @@ __global__ void __launch_bounds__(kQThreads, 1) fused_tc_pair_kernel(const __gri
                     }
                     if (bt_id == 0) {
                         const uint32_t st = smem0 + (uint32_t)(kQSmemA + s * kQBStage);
-                        // this CTA's rows: t in [64 r, 64 r + 64) and 128 + t, two 8 KB blocks
-                        const uint32_t o0 = (uint32_t)(rank * kQBPart), o1 = (uint32_t)(2 * kQBPart + rank * kQBPart);
-                        q_expect(bfull(s), 2u * kQBPart);            // the partner's half lands here
-                        const uint32_t pbar = peer_addr(bfull(s), peer);
-                        q_s2peer(peer_addr(st + o0, peer), st + o0, (uint32_t)kQBPart, pbar);
-                        q_s2peer(peer_addr(st + o1, peer), st + o1, (uint32_t)kQBPart, pbar);
+                        // this CTA's rows: t in [(128/R) r, (128/R)(r + 1)) and 128 + t, two blocks
+                        constexpr uint32_t part = (uint32_t)kQPart<R>;
+                        const uint32_t o0 = rank * part, o1 = (uint32_t)(16 * kQSBO) + rank * part;
+                        q_expect(bfull(s), 2u * (R - 1) * part);     // the other CTAs' parts land here
+#pragma unroll
+                        for (uint32_t d = 1; d < (uint32_t)R; ++d) {
+                            const uint32_t peer = (rank + d) % (uint32_t)R;
+                            const uint32_t pbar = peer_addr(bfull(s), peer);
+                            q_s2peer(peer_addr(st + o0, peer), st + o0, part, pbar);
+                            q_s2peer(peer_addr(st + o1, peer), st + o1, part, pbar);
+                        }
                     }
                 }
             }
@@ -397,7 +456,7 @@ __global__ void __launch_bounds__(kQThreads, 1) fused_tc_pair_kernel(const __gri
         // ------------------------------ up-channel warps ------------------------------
         asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" :: "n"(kQRegUp) : "memory");
         const int q4 = warp & 3;                                   // tensor-memory lane quarter
-        const int ell = 32 * q4 + lane;                            // this thread's bin: 128 rank + ell
+        const int ell = 32 * q4 + lane;                            // this thread's row: 128 rank + ell
         uint32_t p_acc = 0;
         long long pass = 0;
         bool ok = true;
@@ -427,9 +486,19 @@ __global__ void __launch_bounds__(kQThreads, 1) fused_tc_pair_kernel(const __gri
                 if (abort_s) ok = false;
             }
             if (ok) {
-                float* o = sg.out + (long long)(kNs * j + 128 * (int)rank + ell) * sg.beam_stride + F;
+                if constexpr (R == 2) {
+                    float* o = sg.out + (long long)(kNs * j + 128 * (int)rank + ell) * sg.beam_stride + F;
 #pragma unroll
-                for (int q = 0; q < kSub; ++q) o[(long long)q * sg.sub_stride] = acc[q].x + acc[q].y;
+                    for (int q = 0; q < kSub; ++q) o[(long long)q * sg.sub_stride] = acc[q].x + acc[q].y;
+                } else {
+                    // the clamp (Eq. 1): bin 128 r + ell feeds every beam m with L(m) = that bin
+                    const int16_t* inv = bt.inv + (size_t)sg.table * kInvLen;
+                    for (int m = inv[128 * (int)rank + ell]; m >= 0; m = inv[kBins + m]) {
+                        float* o = sg.out + (long long)(kNs * j + m) * sg.beam_stride + F;
+#pragma unroll
+                        for (int q = 0; q < kSub; ++q) o[(long long)q * sg.sub_stride] = acc[q].x + acc[q].y;
+                    }
+                }
             }
         }
         if (!ok) abort_s = 1;
@@ -437,7 +506,7 @@ __global__ void __launch_bounds__(kQThreads, 1) fused_tc_pair_kernel(const __gri
 
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    // the partner's copies into this CTA and out of it are complete before either leaves
+    // the other CTAs' copies into this CTA and out of it are complete before any leaves
     cluster_sync();
     if (abort_s && tid == 0 && bt.status) atomicExch(bt.status, 1);
     if (warp == 0) {
@@ -446,29 +515,9 @@ __global__ void __launch_bounds__(kQThreads, 1) fused_tc_pair_kernel(const __gri
     }
 }
 
-}  // namespace
-
-cudaError_t fused_tc_pair_launch(const Batch& b, int grid, cudaStream_t s) {
-    if (b.n_items <= 0) return cudaSuccess;
-    grid &= ~1;
-    if (grid < 2) grid = 2;
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    static std::once_flag once[kMaxDevices];
-    static cudaError_t result[kMaxDevices];
-    std::call_once(once[dev], [&] {
-        // the register split must fit in what the kernel was launched with (else the
-        // up-channel warps' increase would never be granted): such a build is refused
-        cudaFuncAttributes fa;
-        cudaError_t r = cudaFuncGetAttributes(&fa, fused_tc_pair_kernel);
-        if (r == cudaSuccess && fa.numRegs < kQRegLaunchMin) r = cudaErrorInvalidConfiguration;
-        if (r == cudaSuccess)
-            r = cudaFuncSetAttribute(fused_tc_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kQSmem);
-        result[dev] = r;
-    });
-    if (result[dev] != cudaSuccess) return result[dev];
+// Launch of the R-CTA cluster kernel; grid is a multiple of R.
+template <int R>
+cudaError_t cluster_launch(const Batch& b, int grid, cudaStream_t s) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid);
     cfg.blockDim = dim3(kQThreads);
@@ -476,14 +525,77 @@ cudaError_t fused_tc_pair_launch(const Batch& b, int grid, cudaStream_t s) {
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.x = R;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    e = cudaLaunchKernelEx(&cfg, fused_tc_pair_kernel, b);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, fused_tc_pair_kernel<R>, b);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
+}
+
+// Once per device and cluster size: the register split must fit in what the kernel was
+// launched with (else the up-channel warps' increase could never be granted: such a build
+// is refused), the shared-memory size is set, and the clusters that fit at once are counted.
+template <int R>
+cudaError_t cluster_setup(int* max_clusters) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    static std::once_flag once[kMaxDevices];
+    static cudaError_t result[kMaxDevices];
+    static int clusters[kMaxDevices];
+    std::call_once(once[dev], [&] {
+        cudaFuncAttributes fa;
+        cudaError_t r = cudaFuncGetAttributes(&fa, fused_tc_pair_kernel<R>);
+        if (r == cudaSuccess && fa.numRegs < kQRegLaunchMin) r = cudaErrorInvalidConfiguration;
+        if (r == cudaSuccess)
+            r = cudaFuncSetAttribute(fused_tc_pair_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kQSmem);
+        int sms = 0;
+        if (r == cudaSuccess) r = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        int n = sms / R;
+        if (r == cudaSuccess && R > 2) {
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3((unsigned)(R * n));
+            cfg.blockDim = dim3(kQThreads);
+            cfg.dynamicSmemBytes = kQSmem;
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeClusterDimension;
+            attr[0].val.clusterDim.x = R;
+            attr[0].val.clusterDim.y = 1;
+            attr[0].val.clusterDim.z = 1;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            r = cudaOccupancyMaxActiveClusters(&n, fused_tc_pair_kernel<R>, &cfg);
+        }
+        clusters[dev] = n;
+        result[dev] = r;
+    });
+    *max_clusters = clusters[dev];
+    return result[dev];
+}
+
+}  // namespace
+
+cudaError_t fused_tc_pair_launch(const Batch& b, int grid, cudaStream_t s) {
+    if (b.n_items <= 0) return cudaSuccess;
+    grid &= ~1;
+    if (grid < 2) grid = 2;
+    int max_clusters = 0;
+    cudaError_t e = cluster_setup<2>(&max_clusters);
+    if (e != cudaSuccess) return e;
+    return cluster_launch<2>(b, grid, s);
+}
+
+cudaError_t fused_tc_dft512_launch(const Batch& b, cudaStream_t s) {
+    if (b.n_items <= 0) return cudaSuccess;
+    int max_clusters = 0;
+    cudaError_t e = cluster_setup<4>(&max_clusters);
+    if (e != cudaSuccess) return e;
+    if (max_clusters < 1) return cudaErrorInvalidConfiguration;
+    return cluster_launch<4>(b, 4 * std::min(max_clusters, b.n_items), s);
 }
 
 }  // namespace chimebf

@@ -72,7 +72,15 @@ struct Ticket {
     std::string msg;
     size_t bytes = 0;               // admission accounting
     uint64_t batch = 0;
+    // timeline on the host's monotonic clock (seconds): submitted, its batch launched,
+    // the batch's completion seen by the runtime
+    double t_submit = 0, t_launch = 0, t_done = 0;
+    double t_exec = 0;              // the batch's device time between its start and end events
 };
+
+double now_s() {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
 
 struct Job {
     uint64_t ticket;
@@ -92,6 +100,7 @@ struct TrackBuf {
 struct InflightBatch {
     uint64_t id;
     cudaEvent_t ev;
+    cudaEvent_t ev_start;                               // before the batch's first kernel (timing)
     std::vector<uint64_t> tickets;
     size_t bytes;
     std::vector<std::pair<size_t, uint8_t*>> release;   // carry buffers free once the batch is done
@@ -126,6 +135,9 @@ struct bf_plan_s {
     std::vector<uint64_t> slot_used;          // LRU clock of the slot's last lookup
     uint64_t lru_clock = 0;
     int terms = 0;                            // tensor-core GEMM terms (0: FP32 FFT form)
+    bool dft512 = false;                      // BF_TC_DFT512: all 512 rows, the clamp at the output
+    int16_t* d_inv = nullptr;                 // 512-row form: [table_cap][kInvLen] bin -> beams lists
+    unsigned char* d_a512 = nullptr;          // 512-row form: the one FP16 image of the 512 x 512 DFT matrix
     std::vector<unsigned char*> atc_blocks;   // [kTcBlock][tc_a_bytes(terms)] FP16 twiddle images each
     int* h_status = nullptr;                  // mapped status word written by kernels
     int* d_delays = nullptr;                  // dedispersion delay table (grown on demand)
@@ -222,18 +234,19 @@ int track_alloc(bf_plan_s* p, size_t bytes, TrackBuf* out) {
     return BF_OK;
 }
 
-// Tensor-core twiddle image of one frequency: A[m][2n] = cos, A[m][2n+1] = sin
-// of 2 pi n L(m) / 512 (the clamped rows of the zero-padded DFT, Eq. 1), FP16
+// Tensor-core twiddle image of `rows` rows: A[m][2n] = cos, A[m][2n+1] = sin
+// of 2 pi n L(m) / 512 (the clamped rows of the zero-padded DFT, Eq. 1, with
+// the clamp table as L; all 512 rows of the DFT matrix with L(m) = m), FP16
 // hi (and lo = A - hi), laid out chunk by chunk exactly as the kernel's shared
 // memory operand: 8-row x 16-byte core matrices, k-groups 128 B apart, row
 // groups KC/8 * 128 B apart.
-void tc_image(int terms, const int32_t* lut, std::vector<__half>& img) {
+void tc_image(int terms, const int32_t* lut, int rows, std::vector<__half>& img) {
     const int KC = tc_chunk_k(terms);
-    const size_t oper = (size_t)kNs * KC;                 // halves per chunk
+    const size_t oper = (size_t)rows * KC;                // halves per chunk
     const size_t nch = 2 * kFeed / KC;
     const size_t one = oper * nch;
     img.assign(terms == 3 ? 2 * one : one, __float2half(0.f));
-    for (int m = 0; m < kNs; ++m)
+    for (int m = 0; m < rows; ++m)
         for (int n = 0; n < kFeed; ++n) {
             const long long e = ((long long)n * lut[m]) % kBins;
             const double th = 2.0 * kPi * (double)e / kBins;
@@ -247,6 +260,16 @@ void tc_image(int terms, const int32_t* lut, std::vector<__half>& img) {
                 if (terms == 3) img[one + off] = __double2half(v[c] - (double)__half2float(hi));
             }
         }
+}
+
+// The clamp (Eq. 1) read backwards for the 512-row form: inv[k] = the first beam m with
+// L(m) = k and inv[512 + m] = the next beam after m with the same bin (-1 ends a list).
+void inverse_clamp(const int32_t* lut, int16_t* inv) {
+    for (int i = 0; i < kInvLen; ++i) inv[i] = -1;
+    for (int m = kNs - 1; m >= 0; --m) {
+        inv[kBins + m] = inv[lut[m]];
+        inv[lut[m]] = (int16_t)m;
+    }
 }
 
 uint64_t freq_key(double f) {
@@ -362,6 +385,7 @@ void gather_order(const int32_t* lut, int16_t* order) {
 
 const unsigned char* tc_image(const bf_plan_s* p, int slot) {
     if (!p->terms) return nullptr;
+    if (p->dft512) return p->d_a512;
     return p->atc_blocks[slot / kTcBlock] + (size_t)(slot % kTcBlock) * tc_a_bytes(p->terms);
 }
 
@@ -394,7 +418,7 @@ int table_for(bf_plan_s* p, double f, int* idx) {
     ew_table(p, f, ew);
     int16_t order[kNs];
     gather_order(lut, order);
-    if (p->terms) {
+    if (p->terms && !p->dft512) {
         const int blk = n / kTcBlock;
         if (!p->atc_blocks[blk]) CK(cudaMalloc(&p->atc_blocks[blk], (size_t)kTcBlock * tc_a_bytes(p->terms)));
     }
@@ -403,9 +427,13 @@ int table_for(bf_plan_s* p, double f, int* idx) {
     CK(cudaMemcpy(p->d_lut + (size_t)n * kNs, lut16, sizeof lut16, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(p->d_order + (size_t)n * kNs, order, sizeof order, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(p->d_ew + (size_t)n * kEw * kCyl, ew, sizeof ew, cudaMemcpyHostToDevice));
-    if (p->terms) {
+    if (p->dft512) {
+        int16_t inv[kInvLen];
+        inverse_clamp(lut, inv);
+        CK(cudaMemcpy(p->d_inv + (size_t)n * kInvLen, inv, sizeof inv, cudaMemcpyHostToDevice));
+    } else if (p->terms) {
         std::vector<__half> img;
-        tc_image(p->terms, lut, img);
+        tc_image(p->terms, lut, kNs, img);
         CK(cudaMemcpy(const_cast<unsigned char*>(tc_image(p, n)), img.data(), img.size() * sizeof(__half),
                       cudaMemcpyHostToDevice));
     }
@@ -448,6 +476,7 @@ Batch make_batch(const bf_plan_s* p) {
     Batch b;
     std::memset(&b, 0, sizeof b);
     b.lut = p->d_lut;
+    b.inv = p->d_inv;
     b.order = p->d_order;
     b.ew = p->d_ew;
     b.tw512 = p->d_tw512;
@@ -606,12 +635,32 @@ int launch_jobs(bf_plan_s* p, std::vector<Job>& jobs, size_t bytes) {
                                         p->stream);
         if (e != cudaSuccess) return unhold(cuda_fail(e, "tracking table upload"));
     }
+    // timing events around the batch's device work, from the plan's pool (back to it on failure)
+    struct PooledEvent {
+        bf_plan_s* p;
+        cudaEvent_t ev = nullptr;
+        bool kept = false;
+        ~PooledEvent() {
+            if (ev && !kept) p->event_pool.push_back(ev);
+        }
+    } ev_start{p}, ev_end{p};
+    for (PooledEvent* pe : {&ev_start, &ev_end}) {
+        if (!p->event_pool.empty()) {
+            pe->ev = p->event_pool.back();
+            p->event_pool.pop_back();
+        } else {
+            CK(cudaEventCreate(&pe->ev));
+        }
+    }
+    CK(cudaEventRecord(ev_start.ev, p->stream));
     for (auto& bb : batches) {
         bb.epoch = ++p->launches;
         // a launch of at most half a grid of items runs every item as two halves on two CTAs
         // (the 2-term tensor-core form never splits)
         cudaError_t e;
-        if (p->terms == 1) {
+        if (p->dft512) {
+            e = fused_tc_dft512_launch(bb, p->stream);
+        } else if (p->terms == 1) {
             // the 1-term form runs on CTA pairs, one item per pair at a time
             e = fused_tc_pair_launch(bb, 2 * std::min(p->grid / 2, bb.n_items), p->stream);
         } else {
@@ -643,20 +692,16 @@ int launch_jobs(bf_plan_s* p, std::vector<Job>& jobs, size_t bytes) {
                                  c.n_chan, cudaMemcpyDeviceToDevice, p->stream));
         }
     }
-    cudaEvent_t ev;
-    if (!p->event_pool.empty()) {
-        ev = p->event_pool.back();
-        p->event_pool.pop_back();
-    } else {
-        CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
-    }
-    CK(cudaEventRecord(ev, p->stream));
-    InflightBatch ib{p->next_batch++, ev, {}, bytes, {}, tb, std::move(held)};
+    CK(cudaEventRecord(ev_end.ev, p->stream));
+    ev_start.kept = ev_end.kept = true;
+    InflightBatch ib{p->next_batch++, ev_end.ev, ev_start.ev, {}, bytes, {}, tb, std::move(held)};
+    const double t_launch = now_s();
     for (auto& jb : jobs) {
         ib.tickets.push_back(jb.ticket);
         Ticket& t = p->tickets[jb.ticket];
         t.state = T_INFLIGHT;
         t.batch = ib.id;
+        t.t_launch = t_launch;
     }
     for (auto& c : carries) {
         if (c.drop) {
@@ -678,9 +723,14 @@ bool retire(bf_plan_s* p) {
         if (e == cudaErrorNotReady) break;
         const bool expired = p->h_status && *(volatile int*)p->h_status != 0;
         if (expired) *(volatile int*)p->h_status = 0;
+        const double t_done = now_s();
+        float exec_ms = 0.f;
+        if (e == cudaSuccess && cudaEventElapsedTime(&exec_ms, ib.ev_start, ib.ev) != cudaSuccess) exec_ms = 0.f;
         for (uint64_t t : ib.tickets) {
             auto it = p->tickets.find(t);
             if (it == p->tickets.end()) continue;
+            it->second.t_done = t_done;
+            it->second.t_exec = 1e-3 * exec_ms;
             if (e == cudaSuccess && expired) {
                 it->second.state = T_ERROR;
                 it->second.err = BF_ETIMEDOUT;
@@ -698,6 +748,7 @@ bool retire(bf_plan_s* p) {
         if (ib.track.host) p->track_pool.emplace(ib.track.bytes, ib.track);
         for (int t : ib.slots) release_table(p, t);
         p->event_pool.push_back(ib.ev);
+        p->event_pool.push_back(ib.ev_start);
         p->inflight.pop_front();
         any = true;
     }
@@ -796,10 +847,8 @@ int bf_plan(const bf_config* cfg, bf_plan_t* out) {
     if (!(cfg->feed_spacing_m > 0) || !(cfg->cyl_spacing_m >= 0) || !std::isfinite(cfg->feed_spacing_m) ||
         !std::isfinite(cfg->cyl_spacing_m))
         return fail(BF_EINVAL, "bad spacings");
-    if (cfg->form == BF_TC_DFT512)
-        return fail(BF_EINVAL, "BF_TC_DFT512 is not built: its result equals BF_TC_DFT256 at twice the GEMM work");
     if (cfg->form != BF_FP32_FFT && cfg->form != BF_TC_DFT256 && cfg->form != BF_TC_DFT256_X2 &&
-        cfg->form != BF_TC_DFT256_X1)
+        cfg->form != BF_TC_DFT256_X1 && cfg->form != BF_TC_DFT512)
         return fail(BF_EINVAL, "unknown form");
     if (cfg->mode != BF_MODE_DIRECT && cfg->mode != BF_MODE_SERVING) return fail(BF_EINVAL, "bad mode");
     if (cfg->max_streams < 0) return fail(BF_EINVAL, "negative max_streams");
@@ -809,6 +858,10 @@ int bf_plan(const bf_config* cfg, bf_plan_t* out) {
     std::unique_ptr<bf_plan_s> p(new bf_plan_s);
     p->cfg = *cfg;
     p->terms = cfg->form == BF_TC_DFT256 ? 3 : cfg->form == BF_TC_DFT256_X2 ? 2 : cfg->form == BF_TC_DFT256_X1 ? 1 : 0;
+    if (cfg->form == BF_TC_DFT512) {
+        p->terms = 1;
+        p->dft512 = true;
+    }
     p->ns_sin.resize(kNs);
     p->ew_sin.resize(kEw);
     int prc = fill_pointings(p.get(), cfg);
@@ -847,6 +900,15 @@ int bf_plan(const bf_config* cfg, bf_plan_t* out) {
     CK(cudaMalloc(&p->d_ew, (size_t)p->table_cap * kEw * kCyl * sizeof(float2)));
     CK(cudaMalloc(&p->d_tw512, kBins * sizeof(float2)));
     CK(cudaMalloc(&p->d_tw128, kUp * sizeof(float2)));
+    if (p->dft512) {
+        CK(cudaMalloc(&p->d_inv, (size_t)p->table_cap * kInvLen * sizeof(int16_t)));
+        int32_t all[kBins];
+        for (int k = 0; k < kBins; ++k) all[k] = k;
+        std::vector<__half> img;
+        tc_image(1, all, kBins, img);
+        CK(cudaMalloc(&p->d_a512, img.size() * sizeof(__half)));
+        CK(cudaMemcpy(p->d_a512, img.data(), img.size() * sizeof(__half), cudaMemcpyHostToDevice));
+    }
     std::vector<float2> tw(kBins);
     for (int e = 0; e < kBins; ++e)
         tw[e] = make_float2((float)std::cos(-2.0 * kPi * e / kBins), (float)std::sin(-2.0 * kPi * e / kBins));
@@ -927,6 +989,7 @@ int bf_submit(bf_plan_t p, const bf_request* r, uint64_t* ticket) {
     jb.freqs.assign(r->chan_freq_hz, r->chan_freq_hz + r->n_chan);
     jb.req.chan_freq_hz = jb.freqs.data();
     Ticket t;
+    t.t_submit = now_s();
     t.bytes = request_bytes(r, (int64_t)(r->n_samples / kFrame) + 1, sit == p->streams.end());
     if (p->cfg.mem_budget && t.bytes > p->cfg.mem_budget)
         return fail(BF_ENOMEM, "request larger than the plan's memory budget");
@@ -951,7 +1014,7 @@ int bf_submit(bf_plan_t p, const bf_request* r, uint64_t* ticket) {
     return fits ? BF_OK : BF_EQUEUED;
 }
 
-int bf_poll(bf_plan_t p, uint64_t ticket, int64_t timeout_us, int64_t* n_frames_out) {
+static int poll_ticket(bf_plan_t p, uint64_t ticket, int64_t timeout_us, int64_t* n_frames_out, double* times) {
     if (!p) return fail(BF_EINVAL, "null plan");
     const auto t0 = std::chrono::steady_clock::now();
     std::unique_lock<std::mutex> lk(p->mu);
@@ -960,6 +1023,13 @@ int bf_poll(bf_plan_t p, uint64_t ticket, int64_t timeout_us, int64_t* n_frames_
         if (it == p->tickets.end()) return fail(BF_ENOTICKET, "unknown ticket");
         if (it->second.state == T_INFLIGHT) retire(p);
         it = p->tickets.find(ticket);
+        if ((it->second.state == T_DONE || it->second.state == T_ERROR) && times) {
+            times[0] = it->second.t_submit;
+            times[1] = it->second.t_launch;
+            times[2] = it->second.t_done;
+            times[3] = now_s();
+            times[4] = it->second.t_exec;
+        }
         if (it->second.state == T_DONE) {
             if (n_frames_out) *n_frames_out = it->second.n_frames;
             p->tickets.erase(it);
@@ -976,6 +1046,15 @@ int bf_poll(bf_plan_t p, uint64_t ticket, int64_t timeout_us, int64_t* n_frames_
         // inflight: poll the event; queued: wait for the worker
         p->cv.wait_for(lk, std::chrono::microseconds(it->second.state == T_INFLIGHT ? 10 : 200));
     }
+}
+
+int bf_poll(bf_plan_t p, uint64_t ticket, int64_t timeout_us, int64_t* n_frames_out) {
+    return poll_ticket(p, ticket, timeout_us, n_frames_out, nullptr);
+}
+
+int bf_poll_timed(bf_plan_t p, uint64_t ticket, int64_t timeout_us, int64_t* n_frames_out, double* times) {
+    if (!times) return fail(BF_EINVAL, "null times");
+    return poll_ticket(p, ticket, timeout_us, n_frames_out, times);
 }
 
 int bf_destroy(bf_plan_t p) {
@@ -997,6 +1076,7 @@ int bf_destroy(bf_plan_t p) {
             if (kv.second.carry) cudaFree(kv.second.carry);
         for (auto& ib : p->inflight) {
             cudaEventDestroy(ib.ev);
+            cudaEventDestroy(ib.ev_start);
             for (auto& r : ib.release) cudaFree(r.second);
             if (ib.track.host) p->track_pool.emplace(ib.track.bytes, ib.track);
         }
@@ -1015,6 +1095,8 @@ int bf_destroy(bf_plan_t p) {
     cudaFree(p->d_part);
     cudaFree(p->d_part_tok);
     cudaFree(p->d_park);
+    cudaFree(p->d_inv);
+    cudaFree(p->d_a512);
     for (unsigned char* blk : p->atc_blocks)
         if (blk) cudaFree(blk);
     if (p->d_delays) cudaFree(p->d_delays);
@@ -1182,6 +1264,7 @@ static int debug_fused(bf_plan_t p, double freq_hz, const uint8_t* d_vin, int64_
         return fail(BF_EINVAL, "bad argument (n_samples must be a multiple of 384)");
     if (((uintptr_t)d_vin & 15) != 0) return fail(BF_EINVAL, "vin must be 16-byte aligned");
     if (mode == 2 && !p->terms) return fail(BF_EINVAL, "the GEMM dump needs a tensor-core form");
+    if (p->dft512) return fail(BF_EINVAL, "stage dumps are not built for the 512-row form");
     CK(cudaSetDevice(p->device));
     Batch b = make_batch(p);
     TableHold hold(p);
@@ -1219,6 +1302,7 @@ int bf_debug_gemm(bf_plan_t p, double freq_hz, const uint8_t* d_vin, int64_t n_s
 
 int bf_debug_stall(bf_plan_t p, const uint8_t* d_vin, int64_t wait_ns) {
     if (!p || !d_vin || wait_ns <= 0 || wait_ns > 2000000000LL) return fail(BF_EINVAL, "bad argument");
+    if (p->dft512) return fail(BF_EINVAL, "the stall check is not built for the 512-row form");
     if (((uintptr_t)d_vin & 15) != 0) return fail(BF_EINVAL, "vin must be 16-byte aligned");
     CK(cudaSetDevice(p->device));
     Batch b = make_batch(p);

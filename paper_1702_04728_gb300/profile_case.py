@@ -1,7 +1,7 @@
 """Repeated launches of one fused kernel on a node-slice-sized input, for
 profiler captures (``ncu -k <kernel> -s <n> -c <k>``) and quick timings.
 
-    python -m paper_1702_04728_gb300.profile_case [--form fp32|tc1|tc2|tc3]
+    python -m paper_1702_04728_gb300.profile_case [--form fp32|tc1|tc2|tc3|tc512]
         [--launches N] [--n-chan 4] [--n-samples 49152]
 
 The input is counter-based noise generated on the device (the same generator
@@ -15,7 +15,8 @@ from __future__ import annotations
 import argparse
 import json
 
-FORMS = {"fp32": "BF_FP32_FFT", "tc3": "BF_TC_DFT256", "tc2": "BF_TC_DFT256_X2", "tc1": "BF_TC_DFT256_X1"}
+FORMS = {"fp32": "BF_FP32_FFT", "tc3": "BF_TC_DFT256", "tc2": "BF_TC_DFT256_X2", "tc1": "BF_TC_DFT256_X1",
+         "tc512": "BF_TC_DFT512"}
 NODE_SLICE_HZ = (410e6, 520e6, 650e6, 790e6)
 
 

@@ -75,6 +75,8 @@ def test_bad_geometry_rejected_before_cuda(built_lib):
 def test_null_plan_calls_fail_cleanly(built_lib):
     nf = ctypes.c_int64()
     assert built_lib.bf_poll(None, 1, 0, ctypes.byref(nf)) == B.BF_EINVAL
+    times = (ctypes.c_double * 5)()
+    assert built_lib.bf_poll_timed(None, 1, 0, ctypes.byref(nf), times) == B.BF_EINVAL
     assert built_lib.bf_destroy(None) == B.BF_EINVAL
     assert built_lib.bf_submit(None, None, None) == B.BF_EINVAL
 

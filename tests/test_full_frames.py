@@ -31,7 +31,8 @@ def node_slice(built_lib):
     return raw, list(freqs), ref
 
 
-@pytest.mark.parametrize("form,tol", [(B.BF_FP32_FFT, 1e-5), (B.BF_TC_DFT256, 1e-5), (B.BF_TC_DFT256_X1, 1e-3)])
+@pytest.mark.parametrize("form,tol", [(B.BF_FP32_FFT, 1e-5), (B.BF_TC_DFT256, 1e-5), (B.BF_TC_DFT256_X1, 1e-3),
+                                      (B.BF_TC_DFT512, 1e-3)])
 def test_whole_frames_of_the_node_slice(node_slice, form, tol):
     raw, freqs, ref = node_slice
     vin = torch.from_numpy(raw).cuda()

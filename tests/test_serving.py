@@ -119,6 +119,27 @@ def test_poll_timeout_and_unknown_ticket(built_lib):
         assert e.value.code == B.BF_ENOTICKET
 
 
+def test_request_timeline_is_ordered(built_lib):
+    # bf_poll_timed: submitted <= launched <= completion seen <= collected, for requests that
+    # share batches and for one that waits behind them
+    with B.Plan(mode=B.BF_MODE_SERVING, stream=None) as p:
+        raw = torch.from_numpy(synth.noise_only([520e6], 384 * 32, seed=6)).cuda()
+        outs = [torch.empty(1024, 16, 32, dtype=torch.float32, device="cuda") for _ in range(6)]
+        torch.cuda.synchronize()
+        tickets = [p.submit(raw, [520e6], outs[i], stream_id=20 + i, flags=B.BF_END_OF_STREAM)[1]
+                   for i in range(6)]
+        for t in tickets:
+            rc, nf, tm = p.poll_timed(t)
+            assert rc == B.BF_OK and nf == 32
+            assert tm[0] <= tm[1] <= tm[2] <= tm[3]
+            assert tm[3] - tm[0] < 10.0
+            # the batch's device time fits between its launch and the completion being seen
+            assert 0.0 < tm[4] <= (tm[2] - tm[0]) + 1e-3
+        ref = outs[0].cpu()
+        for o in outs[1:]:
+            assert torch.equal(o.cpu(), ref)
+
+
 def test_destroy_drains_outstanding_work(built_lib):
     raw = torch.from_numpy(synth.noise_only([650e6], 384 * 16, seed=5)).cuda()
     ref_plan = B.Plan()

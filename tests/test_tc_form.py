@@ -8,7 +8,10 @@ output element against the oracle):
 
 * BF_TC_DFT256 (3 terms: twiddles hi+lo, data hi+lo): 1e-5, as the FP32 path;
 * BF_TC_DFT256_X2 (2 terms: twiddles hi, data hi+lo): 1e-3;
-* BF_TC_DFT256_X1 (1 term: twiddles hi, data hi): 1e-3 (measured 3.3-3.5e-4).
+* BF_TC_DFT256_X1 (1 term: twiddles hi, data hi): 1e-3 (measured 3.3-3.5e-4);
+* BF_TC_DFT512 (all 512 rows of the zero-padded transform, 1 term, the clamp
+  applied to the result): 1e-3, and the same values as BF_TC_DFT256_X1, whose
+  rows are the kept rows of the same FP16 matrix.
 """
 import numpy as np
 import pytest
@@ -95,7 +98,49 @@ def test_tc_multichannel_ragged_and_node_slice_sample(built_lib):
     assert rel_err(got, ref) <= FORMS[B.BF_TC_DFT256_X2]
 
 
-def test_tc_dft512_not_built(built_lib):
-    with pytest.raises(B.BfError) as e:
-        B.Plan(form=B.BF_TC_DFT512)
-    assert e.value.code == B.BF_EINVAL
+def test_dft512_point_source(built_lib):
+    # the data of the point-source case (one channel at 600 MHz, 3072 samples) through the
+    # 512 x 256 DFT-matrix GEMM
+    raw, f = synth.config_point_source(0)
+    with B.Plan(form=B.BF_TC_DFT512) as p:
+        out = p.run(dev(raw), list(f)).cpu().numpy()
+    ref = O.beamform(raw, f)
+    err = rel_err(out, ref)
+    assert err <= 1e-3, f"max relative error {err:.3e}"
+    assert int(out.sum(axis=(1, 2)).argmax()) == 939
+
+
+def test_dft512_equals_the_256_row_form(built_lib):
+    # 410 MHz leaves bins that no beam takes; at 600 MHz aliasing gives some bins two beams
+    freqs = [410e6, 600e6, 790e6]
+    assert len(set(O.clamp_lut(600e6).tolist())) < 256
+    assert len(set(O.clamp_lut(410e6).tolist())) == 256
+    raw = synth.noise_only(freqs, 384 * 5 + 77, seed=34)
+    with B.Plan(form=B.BF_TC_DFT512) as p:
+        o512 = p.run(dev(raw), freqs).cpu().numpy()
+    with B.Plan(form=B.BF_TC_DFT256_X1) as p:
+        o256 = p.run(dev(raw), freqs).cpu().numpy()
+    assert o512.shape == (1024, 48, 5)
+    # the kept rows of the 512-row GEMM are the 256-row form's rows: same FP16 operands,
+    # same accumulation order, same epilogue
+    assert np.array_equal(o512, o256)
+    assert rel_err(o512, O.beamform(raw, freqs)) <= 1e-3
+
+
+def test_dft512_streams_carry_and_refused_dumps(built_lib):
+    freqs = [520e6, 650e6]
+    n = 384 * 4 + 200
+    raw = synth.noise_only(freqs, n, seed=35)
+    cut = 384 + 123
+    with B.Plan(form=B.BF_TC_DFT512) as p:
+        a = p.run(dev(raw[:, :cut]), freqs, stream_id=7, flags=0).cpu().numpy()
+        b = p.run(dev(raw[:, cut:]), freqs, stream_id=7, flags=B.BF_END_OF_STREAM).cpu().numpy()
+        vin = dev(raw[0, :384])
+        out = torch.empty(3, 2, 4, 256, 128, 2, dtype=torch.float32, device="cuda")
+        with pytest.raises(B.BfError) as e:
+            B.bf_debug_gemm(p.handle, freqs[0], vin, 384, out)
+        assert e.value.code == B.BF_EINVAL
+        assert B.bf_debug_stall(p.handle, vin, 1000000) == B.BF_EINVAL
+    got = np.concatenate([a, b], axis=2)
+    assert got.shape == (1024, 32, 4)
+    assert rel_err(got, O.beamform(raw, freqs)) <= 1e-3
