@@ -31,6 +31,9 @@ sys.path.insert(0, ROOT)
 
 METRIC = "beamformed input-samples/s & HBM roofline %, FFT vs TC-DFT at stated err; p99 latency"
 WORKLOAD = "node_slice: 4 ch (410/520/650/790 MHz) x 49152 samples x 2048 inputs, DM-500 burst"
+N_CHAN, N_SAMP, N_INPUT = 4, 49152, 2048
+FLOP_PER_SAMPLE = 162.0          # N-S 90 (5 N log2 N at N = 512 per 256 inputs) + E-W 32 + up-channel 35 + detect 5
+BYTES_PER_SAMPLE = 1.0 + 1024 * 16 * 4 / (384 * 2048)   # 1 B in + float32 out
 FORM_NAMES = {"BF_FP32_FFT": "fp32_fft", "BF_TC_DFT256": "tc_dft256_3term",
               "BF_TC_DFT256_X2": "tc_dft256_2term", "BF_TC_DFT256_X1": "tc_dft256_1term",
               "BF_TC_DFT512": "tc_dft512_1term"}
@@ -45,10 +48,6 @@ def bench_config(form: str) -> dict:
     return {"workload": WORKLOAD, "n_chan": N_CHAN, "n_samples": N_SAMP, "n_inputs": N_INPUT,
             "form": FORM_NAMES[form], "output": "float32 [1024][64][128]",
             "l2": "inputs (402.7 MB) larger than L2; no flush"}
-N_CHAN, N_SAMP, N_INPUT = 4, 49152, 2048
-FLOP_PER_SAMPLE = 162.0          # N-S 90 (5 N log2 N at N = 512 per 256 inputs) + E-W 32 + up-channel 35 + detect 5
-BYTES_PER_SAMPLE = 1.0 + 1024 * 16 * 4 / (384 * 2048)   # 1 B in + float32 out
-
 
 
 KERNEL_SOURCES = {
@@ -317,6 +316,7 @@ def cpu_baseline(raw, freqs, gpu_out=None, form_outs=None, frames_per_chan: int 
     for name, o in (form_outs or {}).items():
         got = o[:, :, :frames_per_chan].astype(np.float64)
         res.setdefault("max_rel_err_by_form", {})[name] = float(np.max(np.abs(got - ref) / ref))
+        res.setdefault("rel_l2_err_by_form", {})[name] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
     return res
 
 
@@ -340,6 +340,82 @@ def oracle_one_core(raw, freqs, frames_per_chan: int = 1):
     return {"value": N_CHAN * T * N_INPUT / dt, "unit": "input-samples/s", "cores": 1,
             "sample": f"first {frames_per_chan} frame(s) of each of the {N_CHAN} channels, single-threaded BLAS, "
                       f"{dt:.1f} s"}
+
+
+def precision_run(B, torch, stream, roofline, steps=10):
+    """The precision-form workload: each form's throughput on one 600 MHz channel of
+    49152 samples (device-timed), and its output on the point-source data (one
+    channel at 600 MHz, 3072 samples) for the error against the oracle."""
+    from paper_1702_04728_gb300 import synth
+    T = 49152
+    vin = synth.hash_noise_device(3, 1, T)
+    raw1, f1 = synth.config_point_source(0)
+    vin1 = torch.from_numpy(raw1).cuda()
+    out = torch.empty(1024, 16, T // 384, dtype=torch.float32, device="cuda")
+    runs, outs1 = [], {}
+    for name, fname in FORM_NAMES.items():
+        p = B.Plan(stream=stream, form=getattr(B, name))
+        for _ in range(3):
+            p.poll(p.submit(vin, [600e6], out, stream_id=3, flags=B.BF_END_OF_STREAM)[1])
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        tk = [p.submit(vin, [600e6], out, stream_id=3, flags=B.BF_END_OF_STREAM)[1] for _ in range(steps)]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        for t in tk:
+            p.poll(t)
+        ms = e0.elapsed_time(e1) / steps
+        outs1[fname] = p.run(vin1, list(f1)).cpu().numpy()
+        p.close()
+        runs.append({"form": fname, "ms_per_step": ms, "input_samples_per_s": T * N_INPUT / (ms * 1e-3),
+                     "roofline": roofline(fname, T * N_INPUT, ms)})
+    return {"workload": "1 ch (600 MHz) x 49152 samples x 2048 inputs (100.7 MB); errors on the point-source "
+                        "data (600 MHz, 3072 samples)", "forms": runs}, (raw1, f1, outs1)
+
+
+def precision_errors(raw1, f1, outs1):
+    """Max and relative-L2 error of each form's point-source output against the oracle."""
+    import oracle.chime_fftbf as O
+    ref = O.beamform(raw1, list(f1))
+    res = {}
+    for name, o in outs1.items():
+        d = o.astype(np.float64) - ref
+        res[name] = {"max_rel_err": float(np.max(np.abs(d) / ref)),
+                     "rel_l2_err": float(np.linalg.norm(d) / np.linalg.norm(ref))}
+    return res
+
+
+def cpu_fft_baseline(B, raw, freqs, frames_per_chan: int = 16, gpu_out=None):
+    """FP32 FFT pipeline on the host cores (torch.fft on CPU, all threads): unpack,
+    zero-padded 512-point N-S FFT per (time, cylinder, pol), the clamped bins, E-W
+    phasing, 128-point up-channel FFT per block, detection and the 8 x 3 sums.  The
+    clamp table and E-W phases come from the library's host-side tables; a baseline
+    timing, not a check (the oracle is the check)."""
+    import torch
+    T = frames_per_chan * 384
+    cores = torch.get_num_threads()
+    outs = []
+    t0 = time.perf_counter()
+    for c, f in enumerate(freqs):
+        lut, w = B.bf_debug_tables(float(f))
+        b = torch.from_numpy(np.ascontiguousarray(raw[c, :T])).to(torch.int16)
+        x = torch.complex((b >> 4).float() - 8.0, (b & 15).float() - 8.0).reshape(T, 4, 256, 2)
+        X = torch.fft.fft(x, n=512, dim=2)[:, :, torch.from_numpy(lut).long(), :]      # [T, cyl, m, pol]
+        Bj = torch.einsum("tcmp,jc->tpjm", X, torch.from_numpy(w))                    # [T, pol, j, m]
+        Y = torch.fft.fftshift(torch.fft.fft(Bj.reshape(T // 128, 128, 2, 4, 256), dim=1), dim=1)
+        P = (Y.real ** 2 + Y.imag ** 2).sum(dim=2)                                      # [blk, q', j, m]
+        O = P.reshape(frames_per_chan, 3, 16, 8, 4, 256).sum(dim=(1, 3))                # [F, s, j, m]
+        outs.append(O.permute(2, 3, 1, 0).reshape(1024, 16, frames_per_chan))
+    dt = time.perf_counter() - t0
+    res = {"value": len(freqs) * T * N_INPUT / dt, "unit": "input-samples/s", "cores": cores,
+           "kind": "fp32 fft (torch.fft on cpu)",
+           "sample": f"first {frames_per_chan} frames ({T} samples) of each of the {len(freqs)} channels, {dt:.1f} s"}
+    if gpu_out is not None:
+        got = torch.cat(outs, dim=1).double().numpy()
+        ref = gpu_out[:, :, :frames_per_chan].astype(np.float64)
+        res["max_rel_diff_vs_gpu"] = float(np.max(np.abs(got - ref) / ref))
+    return res
 
 
 def run_reference(args):
@@ -629,6 +705,8 @@ def main():
             "clocks": clocks,
             "fp32_probe": probe,
         }
+        prec, prec_outs = precision_run(B, torch, stream, roofline)
+        line["precision_forms"] = prec
         if args.sweep:
             line["sweep"] = sweep_run(B, torch, stream, ws, roofline)
         if args.serving_seconds > 0:
@@ -641,6 +719,8 @@ def main():
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(raw, freqs, host_out.numpy(), form_outs)
             line["cpu_baseline"]["one_core"] = oracle_one_core(raw, freqs)
+            line["precision_forms"]["errors_vs_oracle"] = precision_errors(*prec_outs)
+            line["cpu_fft_baseline"] = cpu_fft_baseline(B, raw, freqs, gpu_out=host_out.numpy())
         print(json.dumps(line), flush=True)
     plan2.close()
     plan.close()
