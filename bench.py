@@ -601,8 +601,7 @@ def main():
     # Each channel goes in requests of whole frames on one stream (the plan's carry state joins
     # them).  A request holds one wave of work items (SMs / 4 E-W beams frames), so no launch
     # ends with a partial wave; the remainder makes a short first piece for the first channel
-    # (its copy cannot overlap anything) and a short last piece for the others (the last one's
-    # compute is the exposed tail, and it splits into half items).  Channels alternate between
+    # and a short last piece for the others (the last one splits into half items).  Channels alternate between
     # two plans on two streams; the copy of piece i + 1 is issued before piece i's request, so
     # the copy engine never waits for the host.
     copy_s, d2h_s = torch.cuda.Stream(), torch.cuda.Stream()
@@ -620,41 +619,78 @@ def main():
         for k, nfr in enumerate(sched[c]):
             pieces.append((c, k, lo, lo + 384 * nfr, k == len(sched[c]) - 1))
             lo += 384 * nfr
-    outs_p = {(c, k): torch.empty(1024, 16, (hi - lo) // 384, dtype=torch.float32, device="cuda")
-              for c, k, lo, hi, _ in pieces}
-    host_outs_p = {p_: torch.empty(tuple(v.shape), dtype=torch.float32).pin_memory() for p_, v in outs_p.items()}
-    in_ev = {p_[:2]: torch.cuda.Event() for p_ in pieces}
-    done_ev = {p_[:2]: torch.cuda.Event() for p_ in pieces}
+    # Steps follow one another as in a continuous stream: step s uses device input and output
+    # buffers s mod 2, so its copies overlap the previous step's last kernels; events keep a
+    # buffer from being overwritten before the kernels (input) or the device->host copies
+    # (output) of the step two back are done with it.
+    vins = [vin, torch.empty_like(vin)]
+    outs_p = [{(c, k): torch.empty(1024, 16, (hi - lo) // 384, dtype=torch.float32, device="cuda")
+               for c, k, lo, hi, _ in pieces} for _ in range(2)]
+    host_outs_p = {p_: torch.empty(tuple(v.shape), dtype=torch.float32).pin_memory() for p_, v in outs_p[0].items()}
+    in_ev = [{p_[:2]: torch.cuda.Event() for p_ in pieces} for _ in range(2)]
+    done_ev = [{p_[:2]: torch.cuda.Event() for p_ in pieces} for _ in range(2)]
+    d2h_ev = [{p_[:2]: torch.cuda.Event() for p_ in pieces} for _ in range(2)]
+    free_ev = [[torch.cuda.Event(), torch.cuda.Event()] for _ in range(2)]
+    used = [False, False]
 
-    def e2e_step():
+    def e2e_step(sidx, pending):
+        bsel = sidx & 1
+        vb, ob = vins[bsel], outs_p[bsel]
+        if used[bsel]:
+            for ev in free_ev[bsel]:                    # kernels of step sidx - 2 have read vb
+                copy_s.wait_event(ev)
+
         def h2d(i):
             c, k, lo, hi, _ = pieces[i]
             with torch.cuda.stream(copy_s):
-                vin[c, lo:hi].copy_(host_in[c, lo:hi], non_blocking=True)
-                in_ev[(c, k)].record(copy_s)
+                vb[c, lo:hi].copy_(host_in[c, lo:hi], non_blocking=True)
+                in_ev[bsel][(c, k)].record(copy_s)
         h2d(0)
         tk = []
         for i, (c, k, lo, hi, last) in enumerate(pieces):
             if i + 1 < len(pieces):
                 h2d(i + 1)
             pl, st = e2e_plans[c % 2]
-            st.wait_event(in_ev[(c, k)])                # beamform the piece once it has landed
-            _, t = pl.submit(vin[c:c + 1, lo:hi], freqs[c:c + 1], outs_p[(c, k)], stream_id=100 + c,
+            st.wait_event(in_ev[bsel][(c, k)])          # beamform the piece once it has landed
+            if used[bsel]:
+                st.wait_event(d2h_ev[bsel][(c, k)])     # step sidx - 2 has read this output back
+            _, t = pl.submit(vb[c:c + 1, lo:hi], freqs[c:c + 1], ob[(c, k)], stream_id=100 + c,
                              flags=B.BF_END_OF_STREAM if last else 0, n_samples=hi - lo)
-            done_ev[(c, k)].record(st)
+            done_ev[bsel][(c, k)].record(st)
             tk.append((pl, t))
             with torch.cuda.stream(d2h_s):              # device->host of each output as it is done
-                d2h_s.wait_event(done_ev[(c, k)])
-                host_outs_p[(c, k)].copy_(outs_p[(c, k)], non_blocking=True)
-        for pl, t in tk:
+                d2h_s.wait_event(done_ev[bsel][(c, k)])
+                host_outs_p[(c, k)].copy_(ob[(c, k)], non_blocking=True)
+                d2h_ev[bsel][(c, k)].record(d2h_s)
+        free_ev[bsel][0].record(stream)
+        free_ev[bsel][1].record(stream2)
+        used[bsel] = True
+        for pl, t in pending:                           # the previous step's tickets
             pl.poll(t)
-        d2h_s.synchronize()
+        return tk
 
-    e2e_step()
+    def e2e_run(n, sync_each):
+        pend = []
+        for sidx in range(n):
+            pend = e2e_step(sidx, pend)
+            if sync_each:
+                for pl, t in pend:
+                    pl.poll(t)
+                pend = []
+                torch.cuda.synchronize()
+        for pl, t in pend:
+            pl.poll(t)
+        torch.cuda.synchronize()
+
+    e2e_run(2, False)
+    e2e_run(1, True)
     barrier()
     t0 = time.perf_counter()
-    for _ in range(args.e2e_steps):
-        e2e_step()
+    e2e_run(args.e2e_steps, True)
+    barrier()
+    e2e_single_ms = (time.perf_counter() - t0) * 1e3 / args.e2e_steps
+    t0 = time.perf_counter()
+    e2e_run(args.e2e_steps, False)
     barrier()
     e2e_ms = (time.perf_counter() - t0) * 1e3 / args.e2e_steps
     # this box's pinned host -> device copy rate: one copy of the whole input, device-timed
@@ -669,6 +705,7 @@ def main():
     h2d_ms = c0.elapsed_time(c1) / 3
     host_out = torch.cat([torch.cat([host_outs_p[(c, k)] for k in range(len(sched[c]))], dim=2)
                           for c in range(N_CHAN)], dim=1)
+    e2e_equal = bool(torch.equal(host_out, out.cpu()))     # the stream's output, bit for bit
 
     ms_t = torch.tensor([ms, e2e_ms], device="cuda")
     if ws > 1:
@@ -693,12 +730,17 @@ def main():
             "roofline": roof,
             "e2e": {"value": samples * ws / (e2e_ms * 1e-3), "unit": "input-samples/s",
                     "h2d_bytes_per_step": samples, "d2h_bytes_per_step": out.numel() * 4,
-                    "ms_per_step": e2e_ms, "h2d_copy_ms": h2d_ms,
-                    "h2d_copy_GBps": samples / (h2d_ms * 1e-3) / 1e9, "how": f"wall clock; requests of {wave} frames (one wave of "
-                                                  "work items) per channel on one stream, a short first and "
-                                                  "last piece, H2D of the next piece overlapping beamforming "
-                                                  "of the previous one, channels alternating between two "
-                                                  "plans on two streams, D2H of each output"},
+                    "ms_per_step": e2e_ms, "single_step_ms": e2e_single_ms, "h2d_copy_ms": h2d_ms,
+                    "equals_device_output": e2e_equal,
+                    "h2d_copy_GBps": samples / (h2d_ms * 1e-3) / 1e9, "how": f"wall clock over consecutive steps of a continuous stream; "
+                                                  f"requests of {wave} frames (one wave of work items) per "
+                                                  "channel on one stream, a short first and last piece, H2D of "
+                                                  "the next piece overlapping beamforming of the previous one, "
+                                                  "channels alternating between two plans on two streams, D2H "
+                                                  "of each output; device buffers alternate between steps so a "
+                                                  "step's copies overlap the previous step's last kernels; "
+                                                  "single_step_ms: the same with a full synchronisation after "
+                                                  "every step"},
             "gpu_launches": args.steps,
             "forms": form_runs,
             "post": post,
