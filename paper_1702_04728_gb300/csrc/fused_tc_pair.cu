@@ -32,10 +32,11 @@
 // R = 2, half an octet for R = 4; the raw words of the next chunk prefetched
 // into registers), 8-11 (one per tensor-memory lane quarter) run the
 // up-channel passes and detection for one row each, warp 12 issues the MMAs
-// and the A copies.  Hand-offs are mbarriers (and one named barrier among the
-// builders); every wait is bounded by %globaltimer, and on expiry the CTA
-// records the failure and leaves its loops (the other CTAs' waits then expire
-// too).
+// and the A copies.  Hand-offs are mbarriers only (each builder warp sends the
+// blocks it wrote to the other CTAs itself, so the builder warps never wait for
+// one another); every wait is bounded by
+// %globaltimer, and on expiry the CTA records the failure and leaves its loops
+// (the other CTAs' waits then expire too).
 #include "device_common.cuh"
 
 #include <cuda_fp16.h>
@@ -51,12 +52,6 @@ constexpr int kQNCH = 2 * kFeed / kQKC;           // 8 chunks per pass
 constexpr int kQSBO = kQKC / 8 * 128;             // 1024 bytes between 8-row groups of an operand
 constexpr int kQAChunk = 128 * kQKC * 2;          // 16 KB: this CTA's 128 rows of A for one chunk
 constexpr int kQBStage = 256 * kQKC * 2;          // 32 KB: one B chunk (N = 256)
-// B rows built by one CTA of an R-CTA cluster, and the bytes of one of its two blocks
-// (rows t and 128 + t)
-template <int R>
-constexpr int kQRows = 128 / R;
-template <int R>
-constexpr int kQPart = kQRows<R> / 8 * kQSBO;     // 8 KB (R = 2), 4 KB (R = 4)
 constexpr int kQNB = 2;                           // B ring stages
 constexpr int kQBuild = 8;                        // builder warps (a multiple of 4)
 constexpr int kQUp = 4;                           // up-channel warps
@@ -149,19 +144,6 @@ __device__ __forceinline__ void q_s2peer(uint32_t dst_cluster, uint32_t src_cta,
                                          uint32_t mbar_cluster) {
     asm volatile("cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
                  :: "r"(dst_cluster), "r"(src_cta), "r"(bytes), "r"(mbar_cluster) : "memory");
-}
-
-// Named barrier over n threads that also ORs a flag across them, so every thread of
-// the group takes the same decision after it.
-__device__ __forceinline__ bool bar_or_q(int id, int n, bool v) {
-    uint32_t r;
-    asm volatile(
-        "{\n\t.reg .pred pi, po;\n\t"
-        "setp.ne.u32 pi, %1, 0;\n\t"
-        "bar.red.or.pred po, %2, %3, pi;\n\t"
-        "selp.u32 %0, 1, 0, po;\n\t}"
-        : "=r"(r) : "r"((uint32_t)v), "r"(id), "r"(n) : "memory");
-    return r != 0;
 }
 
 __device__ __forceinline__ uint32_t qh2u(__half2 h) { return *reinterpret_cast<uint32_t*>(&h); }
@@ -287,7 +269,7 @@ __global__ void __launch_bounds__(kQThreads, 1) fused_tc_pair_kernel(const __gri
     const uint32_t rank = cluster_rank();
     const uint32_t smem0 = static_cast<uint32_t>(__cvta_generic_to_shared(smem));
     const uint32_t bar0 = static_cast<uint32_t>(__cvta_generic_to_shared(&mbar_s[0]));
-    auto bfull = [&](int s) { return bar0 + 8u * (uint32_t)s; };               // 1 local arrive + the others' parts
+    auto bfull = [&](int s) { return bar0 + 8u * (uint32_t)s; };               // 8 builder warps + the others' parts
     auto bempty = [&](int s) { return bar0 + 8u * (uint32_t)(kQNB + s); };     // every CTA's MMA commit
     auto accfull = [&](int b) { return bar0 + 8u * (uint32_t)(2 * kQNB + b); }; // last commit of a pass
     auto tfree = [&](int b) { return bar0 + 8u * (uint32_t)(2 * kQNB + 2 + b); }; // the up-channel warps
@@ -300,7 +282,7 @@ __global__ void __launch_bounds__(kQThreads, 1) fused_tc_pair_kernel(const __gri
     }
     if (tid == 0) {
         for (int i = 0; i < kQNB; ++i) {
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(bfull(i)) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(bfull(i)), "n"(kQBuild) : "memory");
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(bempty(i)), "n"(R) : "memory");
         }
         for (int i = 0; i < 2; ++i) {
@@ -425,27 +407,35 @@ __global__ void __launch_bounds__(kQThreads, 1) fused_tc_pair_kernel(const __gri
                     }
                     unsigned char* stage = b_ring + s * kQBStage;
                     q_build<R>(cur, sel, w, stage, rank, bt_id);
-                    // the generic-proxy stores are visible to the tensor core and the bulk copy
+                    // the generic-proxy stores are visible to the tensor core and the bulk copies
                     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                    // all builders have written their part; they stop together (an expired wait
-                    // in any of them, or elsewhere in the CTA)
-                    const bool stop = bar_or_q(1, 32 * kQBuild, !ok || abort_s != 0);
-                    if (stop) {
+                    __syncwarp();
+                    // the warp stops as one (an expired wait in any lane, or elsewhere in the CTA)
+                    if (__any_sync(0xffffffffu, !ok || abort_s != 0)) {
                         ok = false;
                         break;
                     }
-                    if (bt_id == 0) {
+                    if (lane == 0) {
+                        // the warp wrote one contiguous block of every 8-row group it touched (a whole
+                        // 1 KB group for R = 2, half of one for R = 4) at rows t and 128 + t: it sends
+                        // them to the other CTAs itself, so no barrier holds the builders together
                         const uint32_t st = smem0 + (uint32_t)(kQSmemA + s * kQBStage);
-                        // this CTA's rows: t in [(128/R) r, (128/R)(r + 1)) and 128 + t, two blocks
-                        constexpr uint32_t part = (uint32_t)kQPart<R>;
-                        const uint32_t o0 = rank * part, o1 = (uint32_t)(16 * kQSBO) + rank * part;
-                        q_expect(bfull(s), 2u * (R - 1) * part);     // the other CTAs' parts land here
+                        uint32_t o0, len;
+                        if constexpr (R == 2) {
+                            o0 = (8u * rank + (uint32_t)warp) * (uint32_t)kQSBO;
+                            len = (uint32_t)kQSBO;
+                        } else {
+                            o0 = (4u * rank + (uint32_t)(warp >> 1)) * (uint32_t)kQSBO + (uint32_t)(warp & 1) * (kQSBO / 2);
+                            len = (uint32_t)kQSBO / 2;
+                        }
+                        const uint32_t o1 = o0 + 16u * (uint32_t)kQSBO;
+                        q_expect(bfull(s), 2u * (R - 1) * len);   // the same warp of each other CTA sends as much
 #pragma unroll
                         for (uint32_t d = 1; d < (uint32_t)R; ++d) {
                             const uint32_t peer = (rank + d) % (uint32_t)R;
                             const uint32_t pbar = peer_addr(bfull(s), peer);
-                            q_s2peer(peer_addr(st + o0, peer), st + o0, part, pbar);
-                            q_s2peer(peer_addr(st + o1, peer), st + o1, part, pbar);
+                            q_s2peer(peer_addr(st + o0, peer), st + o0, len, pbar);
+                            q_s2peer(peer_addr(st + o1, peer), st + o1, len, pbar);
                         }
                     }
                 }
