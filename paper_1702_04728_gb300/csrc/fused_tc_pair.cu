@@ -52,7 +52,7 @@ constexpr int kQNCH = 2 * kFeed / kQKC;           // 8 chunks per pass
 constexpr int kQSBO = kQKC / 8 * 128;             // 1024 bytes between 8-row groups of an operand
 constexpr int kQAChunk = 128 * kQKC * 2;          // 16 KB: this CTA's 128 rows of A for one chunk
 constexpr int kQBStage = 256 * kQKC * 2;          // 32 KB: one B chunk (N = 256)
-constexpr int kQNB = 2;                           // B ring stages
+constexpr int kQNB = 3;                           // B ring stages (225 KB of shared memory in all)
 constexpr int kQBuild = 8;                        // builder warps (a multiple of 4)
 constexpr int kQUp = 4;                           // up-channel warps
 constexpr int kQThreads = 32 * (kQBuild + kQUp + 1);
