@@ -53,7 +53,7 @@ def run_stream(plan, st, out_list, lock=None, budget_wait=False):
     out_list.append((st["id"], torch.cat(outs, dim=2).cpu()))
 
 
-@pytest.mark.parametrize("form", [B.BF_FP32_FFT, B.BF_TC_DFT256])
+@pytest.mark.parametrize("form", [B.BF_FP32_FFT, B.BF_TC_DFT256, B.BF_TC_DFT256_X1, B.BF_TC_DFT512])
 def test_mixed_batches_equal_alone(built_lib, form):
     """In the tensor-core form a mixed batch holds segments of many channel
     frequencies, so the twiddle images change from chunk to chunk within one

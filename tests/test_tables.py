@@ -4,7 +4,8 @@ least recently used one that no open stream and no running batch references.
 
 A serving plan with 64 slots runs 1100 requests of distinct frequencies (more
 than 17 times its slots) with up to 24 in flight, for the FP32 form and the
-1-term tensor-core form; sampled results match the oracle, and a frequency
+1-term tensor-core forms (256 rows: twiddle images per slot; 512 rows: the
+bin-to-beams tables per slot); sampled results match the oracle, and a frequency
 whose slot was refilled many times over gives the same bits as on first use.
 More distinct frequencies than slots in one request fail cleanly.
 """
@@ -25,7 +26,7 @@ def dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
-@pytest.mark.parametrize("form,tol", [(B.BF_FP32_FFT, 1e-5), (B.BF_TC_DFT256_X1, 1e-3)])
+@pytest.mark.parametrize("form,tol", [(B.BF_FP32_FFT, 1e-5), (B.BF_TC_DFT256_X1, 1e-3), (B.BF_TC_DFT512, 1e-3)])
 def test_serving_plan_reuses_table_slots(built_lib, form, tol):
     n_req, in_flight = 1100, 24
     rng = np.random.default_rng(17)
