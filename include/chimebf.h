@@ -274,14 +274,17 @@ int bf_debug_gather_order(const bf_config* cfg, double freq_hz, int16_t* order_o
 int bf_debug_gemm(bf_plan_t p, double freq_hz, const uint8_t* d_vin, int64_t n_samples, float* d_out);
 
 /* Failure-detection check of the device-side waits (no counterpart in the
- * paper): runs the tensor-core kernel on one frame (d_vin: device, 384 x 2048
- * bytes, 16-byte aligned) with its MMA warp idle, so no pipeline stage is ever
- * released, and every mbarrier wait bounded by wait_ns (1 .. 2e9).  The
- * kernel neither traps nor spins unbounded: its waits run out, it frees its
- * tensor memory and reports through the plan's status word, and the call
- * returns BF_ETIMEDOUT, after which the plan and the CUDA context remain
- * usable.  BF_OK would mean a wait did not expire.  Any plan form may call it;
- * it synchronises the plan's stream. */
+ * paper): runs a tensor-core kernel on one frame (d_vin: device, 384 x 2048
+ * bytes, 16-byte aligned) with its MMA thread idle, so no pipeline stage is
+ * ever released, and every mbarrier wait bounded by wait_ns (1 .. 2e9).  The
+ * kernel is the plan's own for the 1-term and 512-row forms (one cluster of
+ * two or four CTAs, which also exchange data-tile copies before their waits
+ * run out) and the single-CTA tensor-core kernel for every other form.  It
+ * neither traps nor spins unbounded: its waits run out, it frees its tensor
+ * memory and reports through the plan's status word, and the call returns
+ * BF_ETIMEDOUT, after which the plan and the CUDA context remain usable.
+ * BF_OK would mean a wait did not expire.  Any plan form may call it; it
+ * synchronises the plan's stream. */
 int bf_debug_stall(bf_plan_t p, const uint8_t* d_vin, int64_t wait_ns);
 
 /* Device unpack of n bytes into 2n floats (re, im), with the same device

@@ -84,6 +84,9 @@ cudaError_t fused_tc_pair_launch(const Batch& b, int grid, cudaStream_t s);
 // The 512-row form (all bins of the zero-padded transform, clamp at the output) on clusters
 // of four CTAs; the grid is the clusters that fit at once.
 cudaError_t fused_tc_dft512_launch(const Batch& b, cudaStream_t s);
+// Stall check of the cluster kernel (cluster 2 or 4 CTAs, one cluster): the MMA thread stays
+// idle, the other waits run out against b.wait_ns and the kernel reports through b.status.
+cudaError_t fused_tc_pair_stall_launch(const Batch& b, int cluster, cudaStream_t s);
 size_t tc_a_bytes(int terms);    // bytes of one table's twiddle image(s)
 cudaError_t skymap_launch(const float* in, int n_beams, long long per_beam, float* map, cudaStream_t s);
 cudaError_t dedisperse_launch(const float* in, const int* delays, int n_sub, long long nf, long long n_out,

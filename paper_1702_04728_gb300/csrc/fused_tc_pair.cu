@@ -255,7 +255,9 @@ __device__ __forceinline__ void q_build(const QRaw<R>& r, uint32_t sel, const Ew
     }
 }
 
-template <int R>
+// kStall: failure-detection check; the MMA thread stays idle, so no stage is ever released and
+// every other wait runs out against the launch's bound.
+template <int R, bool kStall>
 __global__ void __launch_bounds__(kQThreads, 1) fused_tc_pair_kernel(const __grid_constant__ Batch bt) {
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ uint32_t tmem_base_s;
@@ -313,7 +315,7 @@ __global__ void __launch_bounds__(kQThreads, 1) fused_tc_pair_kernel(const __gri
 
     if (warp == kQMmaWarp) {
         // ------------------------------ MMA / copy thread ------------------------------
-        if (lane == 0) {
+        if (lane == 0 && !kStall) {
             uint32_t p_bfull = 0, p_tfree = 0, p_afull = 0, p_adone = 0;
             const unsigned char* a_cur = nullptr;
             long long c = 0, pass = 0;
@@ -496,9 +498,21 @@ __global__ void __launch_bounds__(kQThreads, 1) fused_tc_pair_kernel(const __gri
 
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    // the other CTAs' copies into this CTA and out of it are complete before any leaves
+    // every CTA of the cluster is done issuing copies; in a run that completed, each CTA's MMA
+    // thread has also seen every copy into it land (its last "B full" waits)
     cluster_sync();
-    if (abort_s && tid == 0 && bt.status) atomicExch(bt.status, 1);
+    if (abort_s) {
+        if (tid == 0 && bt.status) atomicExch(bt.status, 1);
+        if (warp == 0) {
+            // after an expired wait, copies that another CTA issued before the cluster barrier
+            // may still be landing in this CTA's shared memory: warp 0 keeps the CTA resident
+            // a while (bounded), then reconverges for the TMEM release
+            const unsigned long long t0 = globaltimer();
+            while (globaltimer() - t0 < 200000ull) {
+            }
+            __syncwarp();
+        }
+    }
     if (warp == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" :: "r"(tmem) : "memory");
@@ -506,7 +520,7 @@ __global__ void __launch_bounds__(kQThreads, 1) fused_tc_pair_kernel(const __gri
 }
 
 // Launch of the R-CTA cluster kernel; grid is a multiple of R.
-template <int R>
+template <int R, bool kStall = false>
 cudaError_t cluster_launch(const Batch& b, int grid, cudaStream_t s) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid);
@@ -520,7 +534,7 @@ cudaError_t cluster_launch(const Batch& b, int grid, cudaStream_t s) {
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    cudaError_t e = cudaLaunchKernelEx(&cfg, fused_tc_pair_kernel<R>, b);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, fused_tc_pair_kernel<R, kStall>, b);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
@@ -528,7 +542,7 @@ cudaError_t cluster_launch(const Batch& b, int grid, cudaStream_t s) {
 // Once per device and cluster size: the register split must fit in what the kernel was
 // launched with (else the up-channel warps' increase could never be granted: such a build
 // is refused), the shared-memory size is set, and the clusters that fit at once are counted.
-template <int R>
+template <int R, bool kStall = false>
 cudaError_t cluster_setup(int* max_clusters) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -539,10 +553,11 @@ cudaError_t cluster_setup(int* max_clusters) {
     static int clusters[kMaxDevices];
     std::call_once(once[dev], [&] {
         cudaFuncAttributes fa;
-        cudaError_t r = cudaFuncGetAttributes(&fa, fused_tc_pair_kernel<R>);
+        cudaError_t r = cudaFuncGetAttributes(&fa, fused_tc_pair_kernel<R, kStall>);
         if (r == cudaSuccess && fa.numRegs < kQRegLaunchMin) r = cudaErrorInvalidConfiguration;
         if (r == cudaSuccess)
-            r = cudaFuncSetAttribute(fused_tc_pair_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kQSmem);
+            r = cudaFuncSetAttribute(fused_tc_pair_kernel<R, kStall>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)kQSmem);
         int sms = 0;
         if (r == cudaSuccess) r = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         int n = sms / R;
@@ -558,7 +573,7 @@ cudaError_t cluster_setup(int* max_clusters) {
             attr[0].val.clusterDim.z = 1;
             cfg.attrs = attr;
             cfg.numAttrs = 1;
-            r = cudaOccupancyMaxActiveClusters(&n, fused_tc_pair_kernel<R>, &cfg);
+            r = cudaOccupancyMaxActiveClusters(&n, fused_tc_pair_kernel<R, kStall>, &cfg);
         }
         clusters[dev] = n;
         result[dev] = r;
@@ -586,6 +601,14 @@ cudaError_t fused_tc_dft512_launch(const Batch& b, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     if (max_clusters < 1) return cudaErrorInvalidConfiguration;
     return cluster_launch<4>(b, 4 * std::min(max_clusters, b.n_items), s);
+}
+
+cudaError_t fused_tc_pair_stall_launch(const Batch& b, int cluster, cudaStream_t s) {
+    if (b.n_items <= 0) return cudaSuccess;
+    int max_clusters = 0;
+    cudaError_t e = cluster == 4 ? cluster_setup<4, true>(&max_clusters) : cluster_setup<2, true>(&max_clusters);
+    if (e != cudaSuccess) return e;
+    return cluster == 4 ? cluster_launch<4, true>(b, 4, s) : cluster_launch<2, true>(b, 2, s);
 }
 
 }  // namespace chimebf

@@ -1302,7 +1302,6 @@ int bf_debug_gemm(bf_plan_t p, double freq_hz, const uint8_t* d_vin, int64_t n_s
 
 int bf_debug_stall(bf_plan_t p, const uint8_t* d_vin, int64_t wait_ns) {
     if (!p || !d_vin || wait_ns <= 0 || wait_ns > 2000000000LL) return fail(BF_EINVAL, "bad argument");
-    if (p->dft512) return fail(BF_EINVAL, "the stall check is not built for the 512-row form");
     if (((uintptr_t)d_vin & 15) != 0) return fail(BF_EINVAL, "vin must be 16-byte aligned");
     CK(cudaSetDevice(p->device));
     Batch b = make_batch(p);
@@ -1316,7 +1315,12 @@ int bf_debug_stall(bf_plan_t p, const uint8_t* d_vin, int64_t wait_ns) {
     b.segs[0].vin = d_vin;
     b.segs[0].n_frames = 1;
     b.wait_ns = (unsigned long long)wait_ns;
-    CK(fused_tc_launch(b, 1, 3, std::min(p->grid, kEw), p->stream));
+    if (p->dft512 || p->terms == 1) {
+        // the form's own kernel: clusters of four (512 rows) or two (256 rows, 1 term)
+        CK(fused_tc_pair_stall_launch(b, p->dft512 ? 4 : 2, p->stream));
+    } else {
+        CK(fused_tc_launch(b, 1, 3, std::min(p->grid, kEw), p->stream));
+    }
     CK(cudaStreamSynchronize(p->stream));
     if (p->h_status && *(volatile int*)p->h_status) {
         *(volatile int*)p->h_status = 0;
