@@ -747,18 +747,22 @@ def main():
             "clocks": clocks,
             "fp32_probe": probe,
         }
-        prec, prec_outs = precision_run(B, torch, stream, roofline)
-        line["precision_forms"] = prec
-        if args.sweep:
+        # the workloads reported beside the headline, and the host baselines, run at N = 1 only:
+        # under torchrun the other ranks' GPUs would be held idle meanwhile
+        extras = ws == 1
+        prec, prec_outs = precision_run(B, torch, stream, roofline) if extras else (None, None)
+        if extras:
+            line["precision_forms"] = prec
+        if args.sweep and extras:
             line["sweep"] = sweep_run(B, torch, stream, ws, roofline)
-        if args.serving_seconds > 0:
+        if args.serving_seconds > 0 and extras:
             cap = samples / (ms * 1e-3)
             line["serving"] = [serving_run(B, torch, cap, ld, args.serving_seconds, form=headline_form)
                                for ld in (0.5, 0.9)]
             # the full-array offered load of 0.8 TB/s of packed voltage, above one GPU's capacity
             line["serving"].append(serving_run(B, torch, cap, 0.8e12 / cap, min(1.0, args.serving_seconds),
                                                form=headline_form))
-        if not args.no_cpu_baseline:
+        if not args.no_cpu_baseline and extras:
             line["cpu_baseline"] = cpu_baseline(raw, freqs, host_out.numpy(), form_outs)
             line["cpu_baseline"]["one_core"] = oracle_one_core(raw, freqs)
             line["precision_forms"]["errors_vs_oracle"] = precision_errors(*prec_outs)
